@@ -1,0 +1,331 @@
+"""Benchmark: particle-steps/s of the large pair cascade on GB300.
+
+Workload (N = 1): the large single cascade -- Nx = 16384, dx = 0.05,
+dt = 0.025, 64 e- + 64 e+ per cell, E0 = 100, gamma_thr = 50, eps_gamma = 20,
+l_pp = 0.5, FP32-mixed, particle cap 5e8 -- advanced through its cascade and
+field screening (``--prep`` steps, untimed) so the timed steps run at full
+multiplicity.  One step = one pass of the whole path: photon conversion,
+gather/push/move/deposit/emission, Ampere update, diagnostics.
+
+value      particle-steps/s over the K timed steps (device clock, inputs
+           resident in HBM; the particle state, several GB, exceeds L2)
+e2e        the same metric through the C ABI with host buffers: the state is
+           uploaded from pinned host memory, every step's record is read back
+           to the host, and the final E/J are read back
+roofline   the particle kernel against the measured HBM copy bandwidth:
+           24 algorithmic bytes per particle-step (int32 cell + FP32 offset +
+           FP32 momentum, read and written)
+cpu_baseline  the FP64 oracle on a bounded slice of the same workload
+
+``--impl reference`` times the oracle (the only reference this method has)
+on the host cores, on an Nx = 512 slice of the same cascade.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s incl. deposit+QED (batched FP32 vs plain FP64), % HBM roofline; p50/p99"
+UNIT = "particle-steps/s"
+BYTES_PER_PARTICLE_STEP = {"fp32": 24, "fp64": 40}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--prep", type=int, default=400, help="untimed steps that grow the cascade")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_slice(steps_prep: int, steps_timed: int):
+    """FP64 oracle on an Nx = 512 slice of the large cascade (same dx, dt,
+    ppc, E0, gamma_thr, eps_gamma, l_pp).  Returns particle-steps/s of the
+    timed steps and what was timed."""
+    import oracle
+    from paper_2012_05587_gb300 import workloads as W
+
+    p = W.large_cascade(precision="fp64")
+    p = {k: v for k, v in p.items() if k not in ("precision", "steps")}
+    p["nx"] = 512
+    p["particle_cap"] = 1 << 26
+    o = oracle.Oracle(p)
+    if steps_prep:
+        o.step(steps_prep)
+    t0 = time.perf_counter()
+    d = o.step(steps_timed)
+    el = time.perf_counter() - t0
+    ps = float((d["n_elec"] + d["n_posi"]).sum())
+    return ps / el, ps, el, (f"FP64 oracle, 1 thread, Nx=512 slice of the large cascade (64+64 per cell), "
+                             f"steps {steps_prep}-{steps_prep + steps_timed}, {ps:.3g} particle-steps in {el:.1f} s")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # the oracle as it stands: prep to the post-screening phase, then W + K steps
+    import oracle
+    from paper_2012_05587_gb300 import workloads as W
+
+    p = W.large_cascade(precision="fp64")
+    p = {k: v for k, v in p.items() if k not in ("precision", "steps")}
+    p["nx"] = 512
+    p["particle_cap"] = 1 << 26
+    o = oracle.Oracle(p)
+    o.step(args.prep)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    d = o.step(args.steps)
+    el = time.perf_counter() - t0
+    ps = float((d["n_elec"] + d["n_posi"]).sum())
+    v = ps / el
+    sample = (f"FP64 oracle, 1 thread, Nx=512 slice of the large cascade, steps "
+              f"{args.prep + args.warmup}-{args.prep + args.warmup + args.steps}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "large cascade slice Nx=512 (64+64 per cell, E0=100, gamma_thr=50, eps=20, "
+                               "l_pp=0.5, dt=0.025, dx=0.05)", "l2": "state fits in host caches; CPU run"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2012_05587_gb300 import Cascade, capi, workloads as W
+
+    prec = args.precision
+    p = W.large_cascade(run=rank, precision=prec)
+    if prec == "fp64":
+        p["particle_cap"] = 150_000_000
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    c = Cascade(p)
+    c.step(args.prep)
+    c.step(args.warmup)
+    c.sync()
+    capi.cascade_set_timing(c.h, True)
+    capi.cascade_timing(c.h)  # clear
+    sampler = ClockSampler(torch.cuda.current_device())
+    barrier()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    c.step(args.steps)
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    tim = capi.cascade_timing(c.h)
+    capi.cascade_set_timing(c.h, False)
+    rec = c.diag(args.steps)
+    c.sync()
+    assert len(rec["step"]) == args.steps
+    ps = float((rec["n_elec"] + rec["n_posi"]).sum())
+    n_now = int(rec["n_elec"][-1] + rec["n_posi"][-1])
+
+    t_max = ms
+    ps_all = ps
+    if world > 1:
+        tt = torch.tensor([ms, ps], dtype=torch.float64, device="cuda")
+        tmax = tt.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_max = float(tmax[0])
+        ps_all = float(tt[1])
+    value = ps_all / (t_max / 1e3)
+
+    peak, peak_kind = measured_peak()
+    bpp = BYTES_PER_PARTICLE_STEP[prec]
+    avg_push_s = tim["particle_kernel_ms"] / 1e3 / max(tim["particle_kernel_launches"], 1)
+    achieved = bpp * ps / args.steps / avg_push_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_push (gather/push/move/deposit/emission)",
+            "bytes_per_particle_step": bpp, "peak_source": peak_kind}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_run(c, p, args.steps, stream, barrier)
+    c.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, psx, el, sample = oracle_slice(150, 60)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"large single cascade {prec}: Nx=16384, dx=0.05, dt=0.025, 64+64 per cell, "
+                                   f"E0=100, gamma_thr=50, eps_gamma=20, l_pp=0.5, steps {args.prep + args.warmup}-"
+                                   f"{args.prep + args.warmup + args.steps} (post-screening)",
+                       "particles_per_step": ps / args.steps, "particles_at_end": n_now,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (particle state >> 129 MB)"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": tim["kernels_launched"] * world,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_run(c, p, steps, stream, barrier):
+    """Same workload through the public API with host buffers: upload the
+    state from pinned host memory (cascade_create_from_state), then every
+    step read its record back (cascade_diag), finally read E and J."""
+    import torch
+
+    from paper_2012_05587_gb300 import Cascade
+
+    cnt = c.counts()
+    ne, npo = cnt["n_elec"], cnt["n_posi"]
+    E, _ = c.fields()
+
+    def pinned(shape, dtype):
+        return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
+
+    host = {}
+    for s, n in ((0, ne), (1, npo)):
+        part = c.particles(s)
+        hc = pinned(n, torch.int32)
+        ho = pinned(n, torch.float64)
+        hu = pinned(n, torch.float64)
+        hc[:] = part["cell"]
+        ho[:] = part["off"]
+        hu[:] = part["u"]
+        host[s] = {"cell": hc, "off": ho, "u": hu}
+    hE = pinned(len(E), torch.float64)
+    hE[:] = E
+    del part
+    barrier()
+    t0 = time.perf_counter()
+    c2 = Cascade(p, state={"elec": host[0], "posi": host[1], "E": hE})
+    ps = 0.0
+    for _ in range(steps):
+        c2.step(1)
+        r = c2.diag(1)
+        ps += float(r["n_elec"][-1] + r["n_posi"][-1])
+    E2, J2 = c2.fields()
+    barrier()
+    el = time.perf_counter() - t0
+    c2.close()
+    h2d = sum(host[s][k].nbytes for s in (0, 1) for k in ("cell", "off", "u")) + hE.nbytes
+    d2h = 112 * steps + E2.nbytes + J2.nbytes
+    return {"value": ps / el, "unit": UNIT, "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "what": "cascade_create_from_state from pinned host arrays + per step cascade_step(1) and "
+                    "cascade_diag(1) to host + final E/J to host; wall clock"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

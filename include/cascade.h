@@ -1,0 +1,189 @@
+/*
+ * cascade.h -- C ABI of the GB300 pair-cascade particle-in-cell library.
+ *
+ * The library advances the 1D periodic electron-positron cascade of
+ * Cruz, Grismayer & Silva, "Kinetic model of large-amplitude oscillations in
+ * neutron star pair cascades" (arXiv:2012.05587), Section 3 setup, with the
+ * simplified QED model of Section 2 (threshold emission, equal split of the
+ * photon energy between the pair), on one CUDA device.
+ *
+ * Units (Section 3): c = 1, time in 1/omega_p, length in c/omega_p, E in
+ * m c omega_p / e, momentum u = p / (m c), density in n0 (per species), with
+ * omega_p^2 = 4 pi e^2 n0 / m.  Then du/dt = q E (q = -1 electrons, +1
+ * positrons), dE/dt = -J (Ampere, Eq. 4 with 4 pi absorbed) and dE/dx = rho.
+ *
+ * Grid: nx cells of size dx, periodic.  Nodes x_i = i dx carry charge; edges
+ * x_{i+1/2} carry E and J; arrays indexed by edge hold E_{i+1/2} at [i].
+ * A particle is stored as an integer cell and an offset in [0, 1).
+ *
+ * Conventions for every entry point:
+ *   - return CASCADE_OK (0) on success, a negative cascade_status otherwise;
+ *   - all pointers named host_* / *_host / out are HOST memory owned by the
+ *     caller; the library owns all device memory it allocates;
+ *   - a failed call leaves the handle valid for cascade_diag, cascade_sync
+ *     and cascade_destroy;
+ *   - work is issued asynchronously on the CUDA stream given at creation
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ */
+#ifndef CASCADE_H
+#define CASCADE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CASCADE_OK = 0,
+  CASCADE_ERR_INVALID_ARG = -1,     /* parameter outside the model's domain, bad pointer or size */
+  CASCADE_ERR_OOM = -2,             /* device allocation failed */
+  CASCADE_ERR_CAPACITY = -3,        /* particle_cap reached: pairs were dropped; results invalid */
+  CASCADE_ERR_CUDA = -4,            /* a CUDA runtime call failed */
+  CASCADE_ERR_TIMEOUT = -5,         /* a bounded device-side wait gave up */
+  CASCADE_ERR_UNIMPLEMENTED = -6,
+  CASCADE_ERR_PHOTON_CAPACITY = -7, /* photon ring full: photons were dropped; results invalid */
+  CASCADE_ERR_BUSY = -8,            /* serving: no free slot or memory budget for the request */
+  CASCADE_ERR_NONFINITE = -9        /* a lepton reached a non-finite energy: the run blew up */
+} cascade_status;
+
+typedef enum { CASCADE_FP64 = 0, CASCADE_FP32_MIXED = 1 } cascade_precision;
+
+/* Parameters of one cascade, as Section 3 states them (plus the photon flight
+ * length l_pp, which generalises the in-place pair creation of Section 2:
+ * l_pp = 0 is the paper's model).
+ * Validity (from the model's physics; otherwise CASCADE_ERR_INVALID_ARG):
+ *   nx >= 2, ppc >= 1, 0 < dt < dx (so |dx per step| < one cell), n0 >= 0,
+ *   u_spread >= 0, eps_gamma >= 2 (pair rest mass), gamma_thr - eps_gamma >= 1
+ *   (the recoiled lepton stays physical), f = eps_gamma / gamma_thr < 2/3
+ *   (the delay (1 - 3f/2) t_a of Eq. 1 is positive), l_pp >= 0. */
+typedef struct {
+  int32_t nx;            /* cells (periodic) */
+  int32_t ppc;           /* seed macro-particles per cell per species */
+  double dx, dt;         /* cell size, time step */
+  double n0;             /* seed density per species; weight w = n0 dx / ppc */
+  double u_spread;       /* seed momenta u ~ Normal(0, u_spread) */
+  uint64_t seed;         /* Philox4x32-10 key for the seed momenta */
+  double E0;             /* initial uniform field */
+  double gamma_thr;      /* emission threshold */
+  double eps_gamma;      /* photon energy in m c^2 (f = eps_gamma / gamma_thr) */
+  double l_pp;           /* photon flight length before conversion */
+  int64_t particle_cap;  /* capacity per species (particles) */
+  int64_t photon_cap;    /* photons in flight; 0 = particle_cap rounded up to a power of 2 */
+  int32_t precision;     /* cascade_precision */
+  int32_t diag_ring;     /* per-step records kept on the device; 0 = 4096 */
+} cascade_params;
+
+/* One record per step, taken after the step (time t = step dt).  Energies are
+ * per unit transverse area in n0 m c^2 (c/omega_p) units. */
+typedef struct {
+  int64_t step;
+  double t;
+  double E_mean;        /* mean of E over edges */
+  double J_mean;        /* mean of J^{n+1/2} over edges */
+  double E_absmax;      /* max |E| */
+  double U_E;           /* sum E^2 / 2 dx */
+  double U_K;           /* sum over leptons of w gamma (rest mass included) */
+  double U_gamma;       /* photons in flight x w x eps_gamma */
+  double gauss_resid;   /* max |E_{i+1/2} - E_{i-1/2} - dx rho_i|; NaN unless computed (cascade_gauss) */
+  int64_t n_elec, n_posi;
+  int64_t n_photon;     /* photons in flight */
+  int64_t n_pairs_total;/* pairs created since the start */
+  int64_t n_emit_multi; /* emissions of more than one photon in one step (dt too coarse) */
+} cascade_diag_t;
+
+typedef struct cascade cascade_t;
+
+/* Device-memory hooks.  alloc returns a device pointer (256-byte aligned) or
+ * NULL; free releases it.  Both receive the cascade's stream and ctx.  When
+ * no hooks are set the library calls cudaMalloc / cudaFree.  The hooks are
+ * global and apply to handles created after the call. */
+typedef void* (*cascade_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*cascade_free_fn)(void* ptr, void* stream, void* ctx);
+int cascade_set_allocator(cascade_alloc_fn alloc_fn, cascade_free_fn free_fn, void* ctx);
+
+/* Create a cascade in the Section 3 initial state: uniform E = E0 on every
+ * edge and, in every cell, ppc co-located e-/e+ pairs (quiet start, rho = 0)
+ * at offsets (k + 1/2)/ppc.  Pair j sits in cell j mod nx, k = j div nx; its
+ * momenta are u_spread * (R cos A, R sin A) with R = sqrt(-2 ln U1),
+ * A = 2 pi U2 (Box-Muller) from one Philox4x32-10 call with counter
+ * (j, 0, 0, 0) and key (seed): U1, U2 are the two 64-bit halves of the
+ * output reduced to 53-bit uniforms in (0, 1).  Electron j gets the cosine
+ * branch, positron j the sine branch. */
+int cascade_create(const cascade_params* params, void* cuda_stream, cascade_t** out);
+
+/* Create a cascade from an explicit state (host arrays, copied): n_elec
+ * electrons and n_posi positrons with cell in [0, nx), offset in [0, 1) and
+ * momentum u; E_host (nx values) is the initial field or NULL for E0. */
+int cascade_create_from_state(const cascade_params* params,
+                              int64_t n_elec, const int32_t* cell_e, const double* off_e, const double* u_e,
+                              int64_t n_posi, const int32_t* cell_p, const double* off_p, const double* u_p,
+                              const double* E_host, void* cuda_stream, cascade_t** out);
+
+/* Advance nsteps steps (asynchronous).  One step n -> n+1 (Sections 2-3):
+ *   1. photons due this step become e-/e+ pairs of gamma = eps_gamma/2 each,
+ *      moving along the photon, at the conversion point x_emit +- l_pp;
+ *   2. every lepton: gather E^n (linear between the two edges around it),
+ *      push u += q dt E, move x += dt u / gamma, deposit the charge-conserving
+ *      current of its linear (CIC) shape;
+ *   3. Ampere: E^{n+1} = E^n - dt J^{n+1/2};
+ *   4. every lepton with gamma >= gamma_thr emits k = 1 + floor((gamma -
+ *      gamma_thr) / eps_gamma) photons and keeps its direction with gamma
+ *      reduced by k eps_gamma; the photons convert n_pp = ceil(l_pp / dt)
+ *      steps later (l_pp = 0: at the start of the next step, in place);
+ *   5. the per-step record.
+ * Errors of earlier asynchronous work (capacity) are reported by the next
+ * cascade_sync / cascade_diag. */
+int cascade_step(cascade_t* h, int32_t nsteps);
+
+/* Wait for the cascade's stream; return the first device-side error seen. */
+int cascade_sync(cascade_t* h);
+
+/* Synchronise, then copy the newest min(max, kept) per-step records, oldest
+ * first, into host_out and their number into n_out.  E_host / J_host (nx
+ * values each, nullable) receive the current E^{n} and the last J^{n-1/2}. */
+int cascade_diag(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t* n_out,
+                 double* E_host, double* J_host);
+
+/* Synchronise and compute Gauss's-law residual max_i |E_{i+1/2} - E_{i-1/2} -
+ * dx rho_i| of the current state (rho from the CIC shape); it is also stored
+ * in the newest per-step record. */
+int cascade_gauss(cascade_t* h, double* resid_out);
+
+/* Synchronise and copy particle counts, photons in flight and the step index. */
+int cascade_counts(cascade_t* h, int64_t* n_elec, int64_t* n_posi, int64_t* n_photon, int64_t* step);
+
+/* Synchronise and copy up to max particles of one species (0 = electrons,
+ * 1 = positrons) in storage order into host arrays (nullable each); n_out
+ * gets the number copied. */
+int cascade_particles(cascade_t* h, int32_t species, int64_t max, int32_t* cell, double* off, double* u,
+                      int64_t* n_out);
+
+/* Kernel timing.  With timing on, cascade_step launches every step directly
+ * (no graph replay) and records a CUDA event pair on the cascade's stream
+ * around each launch of the particle kernel (gather/push/move/deposit/
+ * emission).  cascade_timing synchronises and returns the summed duration
+ * of those launches in milliseconds, their number, and the number of kernels
+ * the library launched while timing was on; it then clears the counters. */
+int cascade_set_timing(cascade_t* h, int32_t enable);
+int cascade_timing(cascade_t* h, double* particle_kernel_ms, int64_t* particle_kernel_launches,
+                   int64_t* kernels_launched);
+
+/* Release all device memory of the handle (NULL is accepted). */
+int cascade_destroy(cascade_t* h);
+
+/* Photon-flight steps n_pp = ceil(l_pp / dt - 1e-9) and device bytes a
+ * cascade with these parameters allocates (for admission by footprint). */
+int cascade_footprint(const cascade_params* params, int32_t* n_pp_out, size_t* device_bytes_out);
+
+/* Human-readable text of a status code (static storage). */
+const char* cascade_status_string(int status);
+
+/* Detail of the last failure on the calling thread (static, thread-local). */
+const char* cascade_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CASCADE_H */

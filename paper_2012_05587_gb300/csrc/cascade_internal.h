@@ -1,0 +1,88 @@
+// Internal types shared by the host side (cascade_capi.cu) and the kernel
+// translation units (kernels_fp64.cu, kernels_fp32.cu).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cascade.h"
+
+namespace cpic {
+
+// Device-resident counters of one cascade.  Every kernel of a step reads the
+// counters it needs from here, so a step has no host synchronisation and a
+// captured CUDA graph of steps can be replayed unchanged.
+struct Ctl {
+  long long n[2];                 // particles per species (0 = e-, 1 = e+)
+  long long ph_head, ph_tail;     // photon FIFO: [ph_head, ph_tail) in flight (monotone)
+  long long pairs_total;          // pairs created since the start
+  long long emit_multi;           // emissions of k > 1 photons
+  long long step;                 // steps completed
+  long long conv_count;           // pairs created by the current step's conversion
+  long long conv_end;             // FIFO head once the current step's photons are converted
+  unsigned long long emit_count;  // photons appended by the current step
+  int err;                        // first device-side error (cascade_status), 0 if none
+  int active_blocks;              // particle-kernel CTAs that work in the current step
+  unsigned int field_ticket;      // last-block detection in the field kernel
+  int pad_;
+};
+
+// Everything a kernel needs about one cascade, passed by value.
+struct Dev {
+  // grid and model constants
+  int nx;              // cells
+  int nxp;             // row pitch of the per-CTA current partials (nx rounded up to 32)
+  int n_pp;            // photon flight in steps
+  int lpp_int;         // floor(l_pp / dx)
+  long long cap;       // particle capacity per species
+  long long ph_cap;    // photon ring capacity (power of two)
+  double dx, dt, dtdx, jscale, w;
+  double gamma_thr, eps_gamma, lpp_frac, u_pair;
+  // particle storage (SoA, one array per species; Real = float or double)
+  int32_t* cell[2];
+  void* off[2];
+  void* u[2];
+  // photon ring: conversion cell (bit 31 = direction is -x) and offset
+  int32_t* ph_cell;
+  void* ph_off;
+  // fields and reduction buffers
+  double* E;           // E_{i+1/2}, nx
+  double* J;           // J_{i+1/2}^{n+1/2}, nx
+  void* S_part;        // per-CTA charge-flux partials, [grid_push][nxp] (Acc)
+  double* S_glob;      // nx, when the partials do not fit in shared memory
+  double* uk_part;     // per-CTA sum of gamma, [grid_push]
+  double* diag_part;   // per-CTA field diagnostics of the field kernel, [grid_field][4]
+  long long* emit_end; // FIFO tail after step m, ring of n_pp + 1
+  Ctl* ctl;
+  cascade_diag_t* ring;
+  int ring_n;
+  int grid_push;       // CTAs of the persistent particle kernel
+  int block_push;      // threads per CTA of the particle kernel
+  int grid_field;      // CTAs of the field kernel
+  int variant;         // particle-kernel variant, see PushVariant
+  long long min_per_cta;  // particles per active CTA before another CTA is woken
+};
+
+enum PushVariant {
+  kSmemESmemS = 0,  // E and the charge-flux accumulator in shared memory
+  kSmemEGlobS = 1,  // E in shared memory, flux through global FP64 atomics
+  kGlobEGlobS = 2,  // both in global memory (very large grids)
+};
+
+constexpr int kFieldBlock = 256;
+
+// Kernel launchers, one set per precision (defined in kernels_fp64.cu and
+// kernels_fp32.cu).  They return a cudaError_t.
+#define CASCADE_DECLARE_LAUNCHERS(SUFFIX)                                                       \
+  cudaError_t seed_##SUFFIX(const Dev& d, long long npairs, int ppc, unsigned long long seed,  \
+                            double u_spread, cudaStream_t s);                                   \
+  cudaError_t step_##SUFFIX(const Dev& d, cudaStream_t s);                                      \
+  cudaError_t step_timed_##SUFFIX(const Dev& d, cudaStream_t s, cudaEvent_t before, cudaEvent_t after); \
+  cudaError_t gauss_##SUFFIX(const Dev& d, double* rho_dx, double* out, cudaStream_t s);       \
+  cudaError_t configure_##SUFFIX(Dev& d, int num_sms);                                         \
+  size_t partial_bytes_##SUFFIX();
+
+CASCADE_DECLARE_LAUNCHERS(fp64)
+CASCADE_DECLARE_LAUNCHERS(fp32)
+
+}  // namespace cpic

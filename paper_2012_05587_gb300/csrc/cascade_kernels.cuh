@@ -1,0 +1,696 @@
+// Device kernels of one pair-cascade PIC step (arXiv:2012.05587, Sections 2-3),
+// templated on the particle precision.  Included by kernels_fp64.cu (built
+// without FMA contraction, so its arithmetic rounds like the plain FP64
+// definition) and kernels_fp32.cu (FP32 particles, FP64 grid reductions).
+//
+// Per step, on one stream:
+//   k_convert  photons due this step -> e-/e+ pairs appended to both species
+//   k_push     persistent grid over all leptons: gather E, push, move,
+//              charge-conserving deposit into a per-CTA shared-memory copy of
+//              the current, threshold emission with warp-aggregated photon
+//              appends; per-CTA current partials and sum(gamma) to global
+//   k_field    FP64 sum of the per-CTA partials in a fixed order, Ampere
+//              update, field diagnostics; its last CTA advances the counters
+//              and writes the per-step record
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "cascade_internal.h"
+
+namespace cpic {
+
+constexpr unsigned kFull = 0xffffffffu;
+// Upper bound on photons one lepton emits in one step (a step that needs more
+// is far too coarse for the model; the count is clamped).
+constexpr int kMaxPhotonsPerStep = 1 << 16;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the 4x32
+// S-box, multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key steps 0x9E3779B9 /
+// 0xBB67AE85.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo0 = 0xD2511F53u * c[0];
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0;
+    const uint32_t n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+__device__ __forceinline__ void set_error(Ctl* ctl, int code) { atomicCAS(&ctl->err, 0, code); }
+
+// ---------------------------------------------------------------------------
+// Seed: quiet start, pair j in cell j mod nx at offset (j div nx + 1/2)/ppc,
+// momenta u_spread * Box-Muller(Philox(counter = (j, 0), key = seed)).
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void k_seed(Dev d, long long npairs, int ppc, unsigned long long seed, double u_spread) {
+  Real* off0 = static_cast<Real*>(d.off[0]);
+  Real* off1 = static_cast<Real*>(d.off[1]);
+  Real* u0 = static_cast<Real*>(d.u[0]);
+  Real* u1 = static_cast<Real*>(d.u[1]);
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < npairs;
+       j += (long long)gridDim.x * blockDim.x) {
+    const int cell = (int)(j % d.nx);
+    const long long k = j / d.nx;
+    const double off = ((double)k + 0.5) / (double)ppc;
+    uint32_t c[4] = {(uint32_t)j, (uint32_t)(j >> 32), 0u, 0u};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const unsigned long long a = ((unsigned long long)c[0] << 32) | c[1];
+    const unsigned long long b = ((unsigned long long)c[2] << 32) | c[3];
+    const double r1 = ((double)(a >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double r2 = ((double)(b >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double rad = sqrt(-2.0 * log(r1));
+    const double ang = 6.283185307179586 * r2;
+    const double ze = rad * cos(ang);
+    const double zp = rad * sin(ang);
+    d.cell[0][j] = cell;
+    d.cell[1][j] = cell;
+    off0[j] = (Real)off;
+    off1[j] = (Real)off;
+    u0[j] = (Real)(u_spread * ze);
+    u1[j] = (Real)(u_spread * zp);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Photon conversion (Section 2: equal split, gamma = eps/2 each, along the
+// photon).  The FIFO holds photons in emission-step order; those emitted at
+// step n - 1 - n_pp end at emit_end[(n - 1 - n_pp) mod (n_pp + 1)].
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void k_convert(Dev d) {
+  Ctl* ctl = d.ctl;
+  const long long step = ctl->step;
+  const long long src = step - 1 - d.n_pp;
+  const long long head = ctl->ph_head;
+  const long long end = (src >= 0) ? d.emit_end[src % (d.n_pp + 1)] : head;
+  const long long n0 = ctl->n[0], n1 = ctl->n[1];
+  long long cnt = end - head;
+  const long long room = min(d.cap - n0, d.cap - n1);
+  const bool over = cnt > room;
+  if (over) cnt = room;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->conv_count = cnt;
+    ctl->conv_end = end;  // photons beyond the capacity are dropped (error below)
+    if (over) set_error(ctl, CASCADE_ERR_CAPACITY);
+    const long long N = n0 + n1 + 2 * cnt;
+    long long g = (N + d.min_per_cta - 1) / d.min_per_cta;
+    if (g < 1) g = 1;
+    if (g > d.grid_push) g = d.grid_push;
+    ctl->active_blocks = (int)g;
+  }
+  const Real up = (Real)d.u_pair;
+  const Real* ph_off = static_cast<const Real*>(d.ph_off);
+  Real* off0 = static_cast<Real*>(d.off[0]);
+  Real* off1 = static_cast<Real*>(d.off[1]);
+  Real* u0 = static_cast<Real*>(d.u[0]);
+  Real* u1 = static_cast<Real*>(d.u[1]);
+  const long long mask = d.ph_cap - 1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long slot = (head + i) & mask;
+    const int enc = d.ph_cell[slot];
+    const int cell = enc & 0x7fffffff;
+    const Real oc = ph_off[slot];
+    const Real uv = (enc < 0) ? -up : up;
+    d.cell[0][n0 + i] = cell;
+    off0[n0 + i] = oc;
+    u0[n0 + i] = uv;
+    d.cell[1][n1 + i] = cell;
+    off1[n1 + i] = oc;
+    u1[n1 + i] = uv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Vector loads of four consecutive particles.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ld4(const int* p, int v[4]) {
+  const int4 t = *reinterpret_cast<const int4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void st4(int* p, const int v[4]) {
+  *reinterpret_cast<int4*>(p) = make_int4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(double* p, const double v[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// ---------------------------------------------------------------------------
+// The particle kernel.  Variant V: see PushVariant.  Acc is the type of the
+// per-CTA shared-memory current accumulator (the precision of the particles).
+// ---------------------------------------------------------------------------
+template <class Real, class Acc, int V>
+__global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  Ctl* ctl = d.ctl;
+  const int G = ctl->active_blocks;
+  if ((int)blockIdx.x >= G) return;
+
+  const int nx = d.nx;
+  Real* Es = reinterpret_cast<Real*>(smem_raw);
+  Acc* Ss = reinterpret_cast<Acc*>(smem_raw + ((nx * sizeof(Real) + 15) & ~size_t(15)));
+  if (V != kGlobEGlobS) {
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) Es[i] = (Real)d.E[i];
+  }
+  if (V == kSmemESmemS) {
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) Ss[i] = Acc(0);
+  }
+  __syncthreads();
+
+  const long long cc = ctl->conv_count;
+  const long long N0 = ctl->n[0] + cc, N1 = ctl->n[1] + cc;
+  const long long C0 = (N0 + 3) >> 2, C1 = (N1 + 3) >> 2, C = C0 + C1;
+  const long long ph_tail = ctl->ph_tail;
+  const long long room = d.ph_cap - (ph_tail - ctl->conv_end);
+  const long long ph_mask = d.ph_cap - 1;
+
+  const Real dt = (Real)d.dt, dtdx = (Real)d.dtdx;
+  const Real thr = (Real)d.gamma_thr, eps = (Real)d.eps_gamma, lpf = (Real)d.lpp_frac;
+  const Real one = Real(1), half = Real(0.5), zero = Real(0);
+  Real* ph_off = static_cast<Real*>(d.ph_off);
+
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const long long stride = (long long)G * blockDim.x;
+  double gsum_total = 0.0;
+
+  for (long long wb = (long long)blockIdx.x * blockDim.x + warp * 32; wb < C; wb += stride) {
+    const long long ch = wb + lane;
+    int s = 0, cnt = 0;
+    long long base = 0;
+    if (ch < C) {
+      s = ch < C0 ? 0 : 1;
+      base = (ch - (s ? C0 : 0)) * 4;
+      const long long N = s ? N1 : N0;
+      cnt = (int)min(4LL, N - base);
+    }
+    int* cellp = d.cell[s] + base;
+    Real* offp = static_cast<Real*>(d.off[s]) + base;
+    Real* up = static_cast<Real*>(d.u[s]) + base;
+    int cl[4] = {0, 0, 0, 0};
+    Real of[4] = {zero, zero, zero, zero}, uu[4] = {zero, zero, zero, zero};
+    if (cnt == 4) {
+      ld4(cellp, cl);
+      ld4(offp, of);
+      ld4(up, uu);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j < cnt) {
+          cl[j] = cellp[j];
+          of[j] = offp[j];
+          uu[j] = up[j];
+        }
+      }
+    }
+    const Real q = s ? one : -one;
+    const Real qdt = s ? dt : -dt;
+    Real gsum = zero;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool valid = j < cnt;
+      int k = 0;
+      int enc = 0;
+      Real oc = zero;
+      if (valid) {
+        const int c = cl[j];
+        const Real o = of[j];
+        // gather: linear between the two edges bracketing the particle
+        int ia, ib;
+        Real w;
+        if (o >= half) {
+          ia = c;
+          ib = (c + 1 == nx) ? 0 : c + 1;
+          w = o - half;
+        } else {
+          ia = (c == 0) ? nx - 1 : c - 1;
+          ib = c;
+          w = o + half;
+        }
+        Real Ea, Eb;
+        if (V == kGlobEGlobS) {
+          Ea = (Real)__ldg(d.E + ia);
+          Eb = (Real)__ldg(d.E + ib);
+        } else {
+          Ea = Es[ia];
+          Eb = Es[ib];
+        }
+        const Real Ep = (one - w) * Ea + w * Eb;
+        // push: du/dt = q E
+        Real u = uu[j] + qdt * Ep;
+        Real g = sqrt(one + u * u);
+        // move: dx/dt = u / gamma, in cell units
+        const Real dd = u / g * dtdx;
+        Real o2 = o + dd;
+        int c2 = c;
+        // charge-conserving deposit: q * (offset change) per edge crossed
+        Acc a1, a2 = Acc(0);
+        int e2 = -1;
+        if (o2 >= one) {
+          a1 = (Acc)(q * (one - o));
+          c2 = (c + 1 == nx) ? 0 : c + 1;
+          o2 = o2 - one;
+          e2 = c2;
+          a2 = (Acc)(q * o2);
+        } else if (o2 < zero) {
+          a1 = (Acc)(q * (zero - o));
+          c2 = (c == 0) ? nx - 1 : c - 1;
+          o2 = o2 + one;
+          e2 = c2;
+          a2 = (Acc)(q * (o2 - one));
+          if (o2 >= one) {
+            o2 = zero;
+            c2 = c;
+          }
+        } else {
+          a1 = (Acc)(q * (o2 - o));
+        }
+        if (V == kSmemESmemS) {
+          atomicAdd(&Ss[c], a1);
+          if (e2 >= 0) atomicAdd(&Ss[e2], a2);
+        } else {
+          atomicAdd(&d.S_glob[c], (double)a1);
+          if (e2 >= 0) atomicAdd(&d.S_glob[e2], (double)a2);
+        }
+        // QED (Section 2): threshold emission with recoil
+        bool emit;
+        const bool fwd = u > zero;  // direction kept through the recoil
+        if (!(g <= Real(1e30))) {
+          // non-finite or absurd gamma: the run has blown up; flag it and do not emit
+          set_error(ctl, CASCADE_ERR_NONFINITE);
+          emit = false;
+        } else if (sizeof(Real) == 4 && g > Real(1e6)) {
+          // large gamma: threshold test and recoil in FP64
+          const double ud = (double)u;
+          const double gd = sqrt(1.0 + ud * ud);
+          emit = gd >= d.gamma_thr;
+          if (emit) {
+            k = 1 + (int)fmin(floor((gd - d.gamma_thr) / d.eps_gamma), (double)kMaxPhotonsPerStep);
+            const double g2 = gd - (double)k * d.eps_gamma;
+            u = (Real)((fwd ? 1.0 : -1.0) * sqrt(g2 * g2 - 1.0));
+            g = (Real)g2;
+          }
+        } else {
+          emit = g >= thr;
+          if (emit) {
+            k = 1 + (int)fmin(floor((g - thr) / eps), (Real)kMaxPhotonsPerStep);
+            const Real g2 = g - (Real)k * eps;
+            const Real sg = fwd ? one : -one;
+            u = sg * sqrt(g2 * g2 - one);
+            g = g2;
+          }
+        }
+        if (emit) {
+          // conversion point x + dir * l_pp, wrapped
+          long long ci;
+          if (fwd) {
+            oc = o2 + lpf;
+            ci = (long long)c2 + d.lpp_int;
+            if (oc >= one) {
+              oc = oc - one;
+              ci += 1;
+            }
+          } else {
+            oc = o2 - lpf;
+            ci = (long long)c2 - d.lpp_int;
+            if (oc < zero) {
+              oc = oc + one;
+              ci -= 1;
+              if (oc >= one) {
+                oc = zero;
+                ci += 1;
+              }
+            }
+          }
+          long long m = ci % nx;
+          if (m < 0) m += nx;
+          enc = (int)m | (fwd ? 0 : (int)0x80000000);
+          if (k > 1) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->emit_multi), 1ull);
+        }
+        cl[j] = c2;
+        of[j] = o2;
+        uu[j] = u;
+        gsum += g;
+      }
+      // warp-aggregated append of this slot's photons
+      const unsigned em = __ballot_sync(kFull, k > 0);
+      if (em) {
+        unsigned long long kk = (unsigned long long)k;
+        unsigned long long incl = kk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long v = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const unsigned long long tot = __shfl_sync(kFull, incl, 31);
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&ctl->emit_count, tot);
+        b0 = __shfl_sync(kFull, b0, 0);
+        const unsigned long long first = b0 + incl - kk;
+        for (int m = 0; m < k; ++m) {
+          const unsigned long long pos = first + m;
+          if ((long long)pos < room) {
+            const long long slot = (ph_tail + (long long)pos) & ph_mask;
+            d.ph_cell[slot] = enc;
+            ph_off[slot] = oc;
+          } else {
+            set_error(ctl, CASCADE_ERR_PHOTON_CAPACITY);
+          }
+        }
+      }
+    }
+    if (cnt == 4) {
+      st4(cellp, cl);
+      st4(offp, of);
+      st4(up, uu);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j < cnt) {
+          cellp[j] = cl[j];
+          offp[j] = of[j];
+          up[j] = uu[j];
+        }
+      }
+    }
+    gsum_total += (double)gsum;
+  }
+
+  // sum of gamma over the CTA (FP64)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gsum_total += __shfl_down_sync(kFull, gsum_total, o);
+  if (lane == 0) red[warp] = gsum_total;
+  __syncthreads();
+  if (warp == 0) {
+    double v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (lane == 0) d.uk_part[blockIdx.x] = v;
+  }
+  if (V == kSmemESmemS) {
+    Acc* P = static_cast<Acc*>(d.S_part) + (size_t)blockIdx.x * d.nxp;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) P[i] = Ss[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Ampere update and field diagnostics; the last CTA finishes the step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_reduce4(double v[4], double* sh /* [4][32] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v[0] += __shfl_down_sync(kFull, v[0], o);
+    v[1] += __shfl_down_sync(kFull, v[1], o);
+    v[2] = fmax(v[2], __shfl_down_sync(kFull, v[2], o));
+    v[3] += __shfl_down_sync(kFull, v[3], o);
+  }
+  if (lane == 0) {
+    sh[warp] = v[0];
+    sh[32 + warp] = v[1];
+    sh[64 + warp] = v[2];
+    sh[96 + warp] = v[3];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    v[0] = lane < nw ? sh[lane] : 0.0;
+    v[1] = lane < nw ? sh[32 + lane] : 0.0;
+    v[2] = lane < nw ? sh[64 + lane] : 0.0;
+    v[3] = lane < nw ? sh[96 + lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v[0] += __shfl_down_sync(kFull, v[0], o);
+      v[1] += __shfl_down_sync(kFull, v[1], o);
+      v[2] = fmax(v[2], __shfl_down_sync(kFull, v[2], o));
+      v[3] += __shfl_down_sync(kFull, v[3], o);
+    }
+  }
+  __syncthreads();
+}
+
+template <class Acc, bool kPartials>
+__global__ void __launch_bounds__(kFieldBlock) k_field(Dev d) {
+  __shared__ double sh[128];
+  __shared__ int s_last;
+  Ctl* ctl = d.ctl;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int G = ctl->active_blocks;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < d.nx) {
+    double S = 0.0;
+    if (kPartials) {
+      const Acc* P = static_cast<const Acc*>(d.S_part) + i;
+      const size_t pitch = d.nxp;
+      int b = 0;
+      for (; b + 4 <= G; b += 4) {
+        const double s0 = (double)P[(size_t)b * pitch];
+        const double s1 = (double)P[(size_t)(b + 1) * pitch];
+        const double s2 = (double)P[(size_t)(b + 2) * pitch];
+        const double s3 = (double)P[(size_t)(b + 3) * pitch];
+        S += s0;
+        S += s1;
+        S += s2;
+        S += s3;
+      }
+      for (; b < G; ++b) S += (double)P[(size_t)b * pitch];
+    } else {
+      S = d.S_glob[i];
+      d.S_glob[i] = 0.0;
+    }
+    const double J = d.jscale * S;
+    const double E = d.E[i] - d.dt * J;
+    d.E[i] = E;
+    d.J[i] = J;
+    v[0] = E;
+    v[1] = J;
+    v[2] = fabs(E);
+    v[3] = 0.5 * E * E * d.dx;
+  }
+  block_reduce4(v, sh);
+  if (threadIdx.x == 0) {
+    double* dp = d.diag_part + 4 * blockIdx.x;
+    dp[0] = v[0];
+    dp[1] = v[1];
+    dp[2] = v[2];
+    dp[3] = v[3];
+    __threadfence();
+    const unsigned t = atomicAdd(&ctl->field_ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last CTA: fold the per-CTA partials in a fixed order
+  double r[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    r[0] += __ldcg(d.diag_part + 4 * b + 0);
+    r[1] += __ldcg(d.diag_part + 4 * b + 1);
+    r[2] = fmax(r[2], __ldcg(d.diag_part + 4 * b + 2));
+    r[3] += __ldcg(d.diag_part + 4 * b + 3);
+  }
+  block_reduce4(r, sh);
+  double gs[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < G; b += blockDim.x) gs[0] += __ldcg(d.uk_part + b);
+  block_reduce4(gs, sh);
+  if (threadIdx.x == 0) {
+    const long long cc = ctl->conv_count;
+    ctl->n[0] += cc;
+    ctl->n[1] += cc;
+    ctl->pairs_total += cc;
+    ctl->ph_head = ctl->conv_end;
+    unsigned long long em = ctl->emit_count;
+    const long long room = d.ph_cap - (ctl->ph_tail - ctl->conv_end);
+    if ((long long)em > room) em = (unsigned long long)room;
+    ctl->ph_tail += (long long)em;
+    d.emit_end[ctl->step % (d.n_pp + 1)] = ctl->ph_tail;
+    ctl->emit_count = 0ull;
+    ctl->conv_count = 0;
+    ctl->step += 1;
+    ctl->field_ticket = 0u;
+    const long long st = ctl->step;
+    cascade_diag_t rec;
+    rec.step = st;
+    rec.t = (double)st * d.dt;
+    rec.E_mean = r[0] / d.nx;
+    rec.J_mean = r[1] / d.nx;
+    rec.E_absmax = r[2];
+    rec.U_E = r[3];
+    rec.U_K = d.w * gs[0];
+    const long long nph = ctl->ph_tail - ctl->ph_head;
+    rec.U_gamma = (double)nph * d.w * d.eps_gamma;
+    rec.gauss_resid = __longlong_as_double(0x7ff8000000000000LL);
+    rec.n_elec = ctl->n[0];
+    rec.n_posi = ctl->n[1];
+    rec.n_photon = nph;
+    rec.n_pairs_total = ctl->pairs_total;
+    rec.n_emit_multi = ctl->emit_multi;
+    d.ring[(st - 1) % d.ring_n] = rec;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gauss's-law residual of the current state (diagnostic, not in the step).
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void k_gauss_deposit(Dev d, double* rho_dx) {
+  Ctl* ctl = d.ctl;
+  const long long N0 = ctl->n[0], N1 = ctl->n[1];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N0 + N1;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int s = t < N0 ? 0 : 1;
+    const long long p = s ? t - N0 : t;
+    const int c = d.cell[s][p];
+    const double o = (double)static_cast<const Real*>(d.off[s])[p];
+    const int c1 = (c + 1 == d.nx) ? 0 : c + 1;
+    const double qw = (s ? 1.0 : -1.0) * d.w;
+    atomicAdd(&rho_dx[c], qw * (1.0 - o));
+    atomicAdd(&rho_dx[c1], qw * o);
+  }
+}
+
+template <class Real>
+__global__ void k_gauss_reduce(Dev d, const double* rho_dx, double* out) {
+  __shared__ double sh[128];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < d.nx; i += blockDim.x) {
+    const int im = (i == 0) ? d.nx - 1 : i - 1;
+    v[2] = fmax(v[2], fabs(d.E[i] - d.E[im] - rho_dx[i]));
+  }
+  block_reduce4(v, sh);
+  if (threadIdx.x == 0) {
+    *out = v[2];
+    const long long st = d.ctl->step;
+    if (st > 0) d.ring[(st - 1) % d.ring_n].gauss_resid = v[2];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (instantiated per precision by the including .cu file).
+// ---------------------------------------------------------------------------
+template <class Real, class Acc>
+struct Launchers {
+  static size_t smem_bytes(int nx, int variant) {
+    const size_t eb = ((size_t)nx * sizeof(Real) + 15) & ~size_t(15);
+    const size_t sb = ((size_t)nx * sizeof(Acc) + 15) & ~size_t(15);
+    if (variant == kSmemESmemS) return eb + sb;
+    if (variant == kSmemEGlobS) return eb;
+    return 0;
+  }
+
+  static const void* push_fn(int variant) {
+    if (variant == kSmemESmemS) return reinterpret_cast<const void*>(&k_push<Real, Acc, kSmemESmemS>);
+    if (variant == kSmemEGlobS) return reinterpret_cast<const void*>(&k_push<Real, Acc, kSmemEGlobS>);
+    return reinterpret_cast<const void*>(&k_push<Real, Acc, kGlobEGlobS>);
+  }
+
+  static cudaError_t configure(Dev& d, int num_sms) {
+    const size_t limit = 200 * 1024;
+    int variant = kGlobEGlobS;
+    if (smem_bytes(d.nx, kSmemESmemS) <= limit) variant = kSmemESmemS;
+    else if (smem_bytes(d.nx, kSmemEGlobS) <= limit) variant = kSmemEGlobS;
+    const size_t smem = smem_bytes(d.nx, variant);
+    const void* fn = push_fn(variant);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int block = 1024;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    d.variant = variant;
+    d.block_push = block;
+    d.grid_push = per_sm * num_sms;
+    d.grid_field = (d.nx + kFieldBlock - 1) / kFieldBlock;
+    d.nxp = (d.nx + 31) & ~31;
+    d.min_per_cta = d.nx > 2048 ? d.nx : 2048;
+    return cudaSuccess;
+  }
+
+  static cudaError_t seed(const Dev& d, long long npairs, int ppc, unsigned long long s, double spread,
+                          cudaStream_t st) {
+    if (npairs <= 0) return cudaSuccess;
+    long long blocks = (npairs + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_seed<Real><<<(int)blocks, 256, 0, st>>>(d, npairs, ppc, s, spread);
+    return cudaGetLastError();
+  }
+
+  // One step: conversion, particle kernel, field kernel.  With events given,
+  // they are recorded around the particle kernel.
+  static cudaError_t step(const Dev& d, cudaStream_t st, cudaEvent_t before = nullptr,
+                          cudaEvent_t after = nullptr) {
+    k_convert<Real><<<d.grid_push, 256, 0, st>>>(d);
+    const size_t smem = smem_bytes(d.nx, d.variant);
+    if (before) cudaEventRecord(before, st);
+    if (d.variant == kSmemESmemS) {
+      k_push<Real, Acc, kSmemESmemS><<<d.grid_push, d.block_push, smem, st>>>(d);
+    } else if (d.variant == kSmemEGlobS) {
+      k_push<Real, Acc, kSmemEGlobS><<<d.grid_push, d.block_push, smem, st>>>(d);
+    } else {
+      k_push<Real, Acc, kGlobEGlobS><<<d.grid_push, d.block_push, 0, st>>>(d);
+    }
+    if (after) cudaEventRecord(after, st);
+    if (d.variant == kSmemESmemS) {
+      k_field<Acc, true><<<d.grid_field, kFieldBlock, 0, st>>>(d);
+    } else {
+      k_field<Acc, false><<<d.grid_field, kFieldBlock, 0, st>>>(d);
+    }
+    return cudaGetLastError();
+  }
+
+  static cudaError_t gauss(const Dev& d, double* rho_dx, double* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(rho_dx, 0, sizeof(double) * d.nx, st);
+    if (e != cudaSuccess) return e;
+    k_gauss_deposit<Real><<<d.grid_push, 256, 0, st>>>(d, rho_dx);
+    k_gauss_reduce<Real><<<1, 1024, 0, st>>>(d, rho_dx, out);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace cpic
+
+#define CASCADE_DEFINE_LAUNCHERS(SUFFIX, REAL, ACC)                                               \
+  namespace cpic {                                                                             \
+  cudaError_t seed_##SUFFIX(const Dev& d, long long npairs, int ppc, unsigned long long seed,    \
+                            double u_spread, cudaStream_t s) {                                    \
+    return Launchers<REAL, ACC>::seed(d, npairs, ppc, seed, u_spread, s);                         \
+  }                                                                                               \
+  cudaError_t step_##SUFFIX(const Dev& d, cudaStream_t s) { return Launchers<REAL, ACC>::step(d, s); } \
+  cudaError_t step_timed_##SUFFIX(const Dev& d, cudaStream_t s, cudaEvent_t b, cudaEvent_t a) {  \
+    return Launchers<REAL, ACC>::step(d, s, b, a);                                                \
+  }                                                                                               \
+  cudaError_t gauss_##SUFFIX(const Dev& d, double* rho_dx, double* out, cudaStream_t s) {         \
+    return Launchers<REAL, ACC>::gauss(d, rho_dx, out, s);                                        \
+  }                                                                                               \
+  cudaError_t configure_##SUFFIX(Dev& d, int num_sms) { return Launchers<REAL, ACC>::configure(d, num_sms); } \
+  size_t partial_bytes_##SUFFIX() { return sizeof(ACC); }                                         \
+  }

@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point that ``include/*.h`` declares, and validates parameters on
+the host (the model's domain, Section 2-3) before any device work."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2012_05587_gb300 import capi, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(cascade_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("cascade_create", "cascade_step", "cascade_diag", "cascade_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = capi.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_sizes_match_the_header_layout():
+    # cascade_params: 2 int32, 9 double, 1 uint64 ... laid out without padding surprises
+    assert ctypes.sizeof(capi.cascade_params) == 4 * 2 + 8 * 9 + 8 * 2 + 4 * 2
+    assert ctypes.sizeof(capi.cascade_diag_t) == 8 * 14
+
+
+@pytest.mark.parametrize("bad,why", [
+    (dict(eps_gamma=1.5), "rest mass"),
+    (dict(gamma_thr=10.5, eps_gamma=10.0), "gamma_thr - eps_gamma"),
+    (dict(gamma_thr=12.0, eps_gamma=9.0), "2/3"),
+    (dict(dt=0.2), "dt"),
+    (dict(nx=1), "nx"),
+    (dict(l_pp=-1.0), "l_pp"),
+    (dict(precision=7), "precision"),
+])
+def test_host_validation(bad, why):
+    p = dict(W.small_cascade(), **bad)
+    with pytest.raises(capi.CascadeError) as ei:
+        capi.cascade_footprint(p)
+    assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
+    assert why in str(ei.value)
+
+
+def test_footprint_and_flight_steps():
+    npp, b = capi.cascade_footprint(W.small_cascade())
+    assert npp == 20                       # ceil(l_pp / dt) = ceil(1.0 / 0.05)
+    npp2, _ = capi.cascade_footprint(dict(W.small_cascade(), l_pp=0.0))
+    assert npp2 == 0
+    p = W.large_cascade()
+    npp3, big = capi.cascade_footprint(p)
+    assert npp3 == 20
+    # particle storage dominates: 2 species x 12 B x cap in FP32-mixed mode
+    assert 2 * 12 * p["particle_cap"] <= big <= 2 * 12 * p["particle_cap"] * 1.5
+    _, big64 = capi.cascade_footprint(dict(p, precision="fp64"))
+    assert big64 > big
+
+
+def test_status_strings():
+    assert capi.status_string(capi.CASCADE_ERR_CAPACITY) == "particle capacity exceeded"
+    assert capi.status_string(12345) == "unknown status"
+
+
+def test_create_without_device_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    with pytest.raises(capi.CascadeError) as ei:
+        capi.cascade_create(W.small_cascade())
+    assert ei.value.status == capi.CASCADE_ERR_CUDA

@@ -1,0 +1,264 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+FP64 mode: per-step records and E/J profiles to relative 1e-5 until the
+parity horizon (the first step where an integer count -- pairs, photons --
+differs: after it the instability of Section 5 amplifies round-off and any
+trajectory is valid).  FP32-mixed mode: ensemble diagnostics to 2%.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2012_05587_gb300 import Cascade, CascadeError, workloads as W
+from paper_2012_05587_gb300 import capi
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5  # FP64 per-step parity tolerance on E and J
+
+
+def oracle_params(p):
+    return {k: v for k, v in p.items() if k not in ("precision", "steps", "photon_cap", "diag_ring")}
+
+
+def run_both(p, steps, chunk):
+    """Advance oracle and GPU side by side; return per-step records and, at
+    every chunk boundary, the E/J profiles of both."""
+    ref = oracle.Oracle(oracle_params(p))
+    recs_ref, recs_gpu, snaps = [], [], []
+    with Cascade(p) as c:
+        done = 0
+        while done < steps:
+            k = min(chunk, steps - done)
+            recs_ref.append(ref.step(k))
+            c.step(k)
+            recs_gpu.append(c.diag(k))
+            E, J = c.fields()
+            E_ref, J_ref = ref.fields()
+            done += k
+            snaps.append((done, E, J, E_ref, J_ref))
+    cat = lambda rs: {f: np.concatenate([r[f] for r in rs]) for f in rs[0]}
+    return cat(recs_ref), cat(recs_gpu), snaps
+
+
+def horizon(r_ref, r_gpu):
+    """First step (1-based) where an integer count differs; len+1 if none."""
+    bad = np.zeros(len(r_ref["step"]), bool)
+    for f in ("n_elec", "n_posi", "n_photon", "n_pairs_total"):
+        bad |= r_ref[f] != r_gpu[f]
+    idx = np.flatnonzero(bad)
+    return int(r_ref["step"][idx[0]]) if len(idx) else len(bad) + 1
+
+
+def check_fp64_parity(p, steps, chunk, min_horizon):
+    r_ref, r_gpu, snaps = run_both(p, steps, chunk)
+    assert np.array_equal(r_gpu["step"], r_ref["step"])
+    hz = horizon(r_ref, r_gpu)
+    assert hz >= min_horizon, f"parity horizon at step {hz}"
+    m = r_ref["step"] < hz
+    Es = max(np.abs(r_ref["E_absmax"][m]).max(), 1e-300)
+    Js = max(np.abs(r_ref["J_mean"][m]).max(), np.abs(r_ref["E_mean"][m]).max() * 1e-3, 1e-300)
+    assert np.abs(r_gpu["E_mean"][m] - r_ref["E_mean"][m]).max() <= RTOL * Es
+    assert np.abs(r_gpu["E_absmax"][m] - r_ref["E_absmax"][m]).max() <= RTOL * Es
+    assert np.abs(r_gpu["J_mean"][m] - r_ref["J_mean"][m]).max() <= RTOL * Js
+    for f in ("U_E", "U_K", "U_gamma"):
+        scale = max(np.abs(r_ref[f][m]).max(), 1e-300)
+        assert np.abs(r_gpu[f][m] - r_ref[f][m]).max() <= RTOL * scale, f
+    checked = 0
+    for done, E, J, E_ref, J_ref in snaps:
+        if done >= hz:
+            break
+        sE = max(np.abs(E_ref).max(), 1e-300)
+        sJ = max(np.abs(J_ref).max(), 1e-300)
+        assert np.abs(E - E_ref).max() <= RTOL * sE, f"E at step {done}"
+        assert np.abs(J - J_ref).max() <= RTOL * sJ, f"J at step {done}"
+        checked += 1
+    assert checked >= 1
+    return hz, r_ref, r_gpu
+
+
+# --- initial state -------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_seed_state_matches_oracle(precision):
+    p = dict(W.small_cascade(), precision=precision)
+    ref = oracle.Oracle(oracle_params(p)).particles()
+    with Cascade(p) as c:
+        for s in (0, 1):
+            g = c.particles(s)
+            assert np.array_equal(g["cell"], ref["cell"][s::2])
+            if precision == "fp64":
+                assert np.array_equal(g["off"], ref["off"][s::2])
+                np.testing.assert_allclose(g["u"], ref["u"][s::2], rtol=1e-14, atol=1e-18)
+            else:
+                assert np.array_equal(g["off"], ref["off"][s::2].astype(np.float32).astype(np.float64))
+                np.testing.assert_allclose(g["u"], ref["u"][s::2].astype(np.float32), rtol=2e-7, atol=1e-12)
+        d = c.diag(1)
+        assert len(d["step"]) == 0
+
+
+# --- FP64 per-step parity ----------------------------------------------------------------
+
+def test_fp64_parity_small_cascade():
+    """The small cascade (Nx = 256, 16 + 16 per cell, l_pp = 1, 1000 steps)."""
+    p = W.small_cascade()
+    hz, r_ref, r_gpu = check_fp64_parity(p, p["steps"], 25, min_horizon=150)
+    print(f"parity horizon: step {hz} of {p['steps']}")
+    # ensemble quantities agree over the whole run
+    assert abs(r_gpu["n_pairs_total"][-1] - r_ref["n_pairs_total"][-1]) <= 0.02 * r_ref["n_pairs_total"][-1]
+
+
+@pytest.mark.parametrize("nx,ppc,lpp", [(300, 3, 0.37), (97, 5, 0.0), (1031, 2, 2.5)])
+def test_fp64_parity_ragged_grids(nx, ppc, lpp):
+    """Grids that are not multiples of the tile or warp sizes, particle counts
+    that are not multiples of four, in-place (l_pp = 0) and long flights."""
+    p = dict(nx=nx, ppc=ppc, dx=0.07, dt=0.03, n0=1.0, u_spread=0.05, seed=11 + nx, E0=12.0,
+             gamma_thr=20.0, eps_gamma=8.0, l_pp=lpp, particle_cap=1 << 16, precision="fp64")
+    check_fp64_parity(p, 400, 20, min_horizon=60)
+
+
+def test_fp64_hand_built_emission_is_exact():
+    """One positron crossing gamma_thr in a frozen field: the emission step,
+    photon flight and the pair agree exactly with the oracle."""
+    p = dict(nx=400, ppc=1, dx=0.1, dt=0.01, n0=1e-14, u_spread=0.0, seed=1, E0=1.0, gamma_thr=20.0,
+             eps_gamma=4.0, l_pp=0.55, particle_cap=64, precision="fp64")
+    ref = oracle.Oracle.from_state(oracle_params(p), [50], [0.3], [19.0], [1])
+    state = {"elec": {"cell": [], "off": [], "u": []}, "posi": {"cell": [50], "off": [0.3], "u": [19.0]}}
+    with Cascade(p, state=state) as c:
+        d_ref = ref.step(200)
+        c.step(200)
+        d = c.diag(200)
+        for f in ("n_elec", "n_posi", "n_photon", "n_pairs_total"):
+            assert np.array_equal(d[f], d_ref[f]), f
+        assert d_ref["n_pairs_total"][-1] == 1
+        pr = ref.particles()
+        e, q = c.particles(0), c.particles(1)
+        assert e["cell"][0] == pr["cell"][1] and e["off"][0] == pr["off"][1] and e["u"][0] == pr["u"][1]
+        assert q["cell"][0] == pr["cell"][0] and q["off"][0] == pr["off"][0] and q["u"][0] == pr["u"][0]
+        assert q["cell"][1] == pr["cell"][2] and q["off"][1] == pr["off"][2] and q["u"][1] == pr["u"][2]
+
+
+def test_gauss_law_on_gpu():
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-4)):
+        p = dict(W.small_cascade(), precision=prec)
+        with Cascade(p) as c:
+            c.step(500)
+            r = c.gauss()
+            E, _ = c.fields()
+            assert r <= tol * max(np.abs(E).max(), 1.0), (prec, r)
+            d = c.diag(1)
+            assert d["gauss_resid"][-1] == r
+
+
+def test_graph_replay_matches_single_steps():
+    p = W.small_cascade()
+    with Cascade(p) as a, Cascade(p) as b:
+        a.step(48)                 # three captured 16-step graphs
+        for _ in range(48):
+            b.step(1)              # direct launches
+        Ea, Ja = a.fields()
+        Eb, Jb = b.fields()
+        np.testing.assert_allclose(Ea, Eb, rtol=0, atol=1e-12 * np.abs(Ea).max())
+        assert a.counts() == b.counts()
+
+
+# --- FP32-mixed ensemble parity -------------------------------------------------------------
+
+def _ensemble(d, E_first_zero_window=200):
+    t = d["t"]
+    E = d["E_mean"]
+    sign = np.signbit(E)
+    z = np.flatnonzero(sign[1:] != sign[:-1])
+    per = 2 * np.mean(np.diff(t[z])) if len(z) > 2 else np.nan
+    return {
+        "pairs": d["n_pairs_total"][-1],
+        "peak_after_screen": np.abs(E[z[0]:]).max() if len(z) else np.nan,
+        "period": per,
+        "energy": (d["U_E"] + d["U_K"] + d["U_gamma"])[-1],
+        "first_zero": t[z[0]] if len(z) else np.nan,
+    }
+
+
+def test_fp32_mixed_ensemble_small_cascade():
+    """FP32-mixed vs the FP64 oracle on ensemble diagnostics (2%): final pair
+    count, screening time, peak field after screening, oscillation period,
+    final energy -- averaged over seeds."""
+    keys = ("pairs", "peak_after_screen", "period", "energy", "first_zero")
+    g_all, r_all = [], []
+    for run in range(4):
+        p = W.small_cascade(run=run, precision="fp32")
+        d_ref = oracle.Oracle(oracle_params(p)).step(p["steps"])
+        with Cascade(p) as c:
+            c.step(p["steps"])
+            d = c.diag(p["steps"])
+        g_all.append(_ensemble(d))
+        r_all.append(_ensemble(d_ref))
+    for k in keys:
+        g = np.mean([x[k] for x in g_all])
+        r = np.mean([x[k] for x in r_all])
+        assert g == pytest.approx(r, rel=0.02), k
+
+
+# --- full-size configuration: first steps against the oracle -------------------------------
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-5), ("fp32", 2e-4)])
+def test_large_cascade_first_steps(precision, tol):
+    """Nx = 16384, 64 + 64 per cell: the launch configuration of the benchmark.
+    60 steps include the first emissions (t_a = 0.5 = 20 steps) and the first
+    conversions (n_pp = 20).  Compared on E/J and on a sample of particles."""
+    p = W.large_cascade(precision=precision)
+    p["particle_cap"] = 1 << 23
+    steps = 60
+    ref = oracle.Oracle(oracle_params(p))
+    d_ref = ref.step(steps)
+    E_ref, J_ref = ref.fields()
+    pr = ref.particles()
+    with Cascade(p) as c:
+        c.step(steps)
+        d = c.diag(steps)
+        E, J = c.fields()
+        assert np.abs(E - E_ref).max() <= tol * np.abs(E_ref).max()
+        assert np.abs(J - J_ref).max() <= tol * max(np.abs(J_ref).max(), 1e-300) * 10
+        assert abs(d["n_pairs_total"][-1] - d_ref["n_pairs_total"][-1]) <= 0.01 * max(d_ref["n_pairs_total"][-1], 1)
+        if precision == "fp64":
+            assert np.array_equal(d["n_photon"], d_ref["n_photon"])
+        rng = np.random.default_rng(5)
+        nseed = 16384 * 64
+        idx = rng.choice(nseed, 4096, replace=False)
+        for s in (0, 1):
+            g = c.particles(s)
+            xg = g["cell"][idx] + g["off"][idx]
+            xr = pr["cell"][2 * idx + s] + pr["off"][2 * idx + s]
+            dxp = (xg - xr + 8192) % 16384 - 8192
+            assert np.abs(dxp).max() <= (1e-9 if precision == "fp64" else 5e-3)
+            np.testing.assert_allclose(g["u"][idx], pr["u"][2 * idx + s], rtol=tol, atol=tol)
+
+
+# --- errors ------------------------------------------------------------------------------------
+
+def test_capacity_overflow_is_reported():
+    p = dict(W.small_cascade(), particle_cap=256 * 16 + 100)
+    with Cascade(p) as c:
+        c.step(200)
+        with pytest.raises(CascadeError) as ei:
+            c.sync()
+        assert ei.value.status == capi.CASCADE_ERR_CAPACITY
+        assert c.counts is not None  # the handle stays usable for diagnostics
+        with pytest.raises(CascadeError):
+            c.diag(10)
+
+
+def test_invalid_parameters_rejected_before_device_work():
+    with pytest.raises(CascadeError) as ei:
+        Cascade(dict(W.small_cascade(), dt=0.2))
+    assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
+
+
+def test_species_counts_and_pair_bookkeeping():
+    p = W.small_cascade()
+    with Cascade(p) as c:
+        c.step(600)
+        d = c.diag(600)
+        seed = p["nx"] * p["ppc"]
+        assert np.array_equal(d["n_elec"], d["n_posi"])
+        assert np.array_equal(d["n_elec"], seed + d["n_pairs_total"])
