@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cap", type=int, default=0, help="particle cap per species (0 = the workload's)")
+    ap.add_argument("--ppc", type=int, default=0, help="seed particles per cell per species (0 = the workload's)")
     return ap.parse_args()
 
 
@@ -194,6 +196,10 @@ def main():
     p = W.large_cascade(run=rank, precision=prec)
     if prec == "fp64":
         p["particle_cap"] = 150_000_000
+    if args.cap:
+        p["particle_cap"] = args.cap
+    if args.ppc:
+        p["ppc"] = args.ppc
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -262,7 +268,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": f"large single cascade {prec}: Nx=16384, dx=0.05, dt=0.025, 64+64 per cell, "
+            "config": {"workload": f"large single cascade {prec}: Nx=16384, dx=0.05, dt=0.025, "
+                                   f"{p['ppc']}+{p['ppc']} per cell, "
                                    f"E0=100, gamma_thr=50, eps_gamma=20, l_pp=0.5, steps {args.prep + args.warmup}-"
                                    f"{args.prep + args.warmup + args.steps} (post-screening)",
                        "particles_per_step": ps / args.steps, "particles_at_end": n_now,

@@ -48,7 +48,15 @@ typedef enum {
   CASCADE_ERR_NONFINITE = -9        /* a lepton reached a non-finite energy: the run blew up */
 } cascade_status;
 
-typedef enum { CASCADE_FP64 = 0, CASCADE_FP32_MIXED = 1 } cascade_precision;
+/* CASCADE_FP64: every particle and grid quantity in FP64.
+ * CASCADE_FP32_MIXED: int32 cell + FP32 offset and momentum; the per-CTA
+ *   current is accumulated in int32 fixed point at a scale chosen per launch
+ *   so no sum can overflow (resolution 2^-10 or finer per contribution at the
+ *   largest sizes), then summed over CTAs, applied to E and reduced for the
+ *   diagnostics in FP64; the threshold test of leptons above gamma = 1e6 is FP64.
+ * CASCADE_FP32_MIXED_FINE: as FP32_MIXED with a two-word accumulator
+ *   (resolution about 2^-20 per contribution, one more atomic each). */
+typedef enum { CASCADE_FP64 = 0, CASCADE_FP32_MIXED = 1, CASCADE_FP32_MIXED_FINE = 2 } cascade_precision;
 
 /* Parameters of one cascade, as Section 3 states them (plus the photon flight
  * length l_pp, which generalises the in-place pair creation of Section 2:

@@ -28,6 +28,7 @@ CASCADE_ERR_NONFINITE = -9
 
 CASCADE_FP64 = 0
 CASCADE_FP32_MIXED = 1
+CASCADE_FP32_MIXED_FINE = 2
 
 
 class cascade_params(ctypes.Structure):
@@ -127,7 +128,8 @@ def check(where: str, status: int) -> None:
 def make_params(p: dict) -> cascade_params:
     prec = p.get("precision", CASCADE_FP64)
     if isinstance(prec, str):
-        prec = {"fp64": CASCADE_FP64, "fp32": CASCADE_FP32_MIXED, "fp32_mixed": CASCADE_FP32_MIXED}[prec]
+        prec = {"fp64": CASCADE_FP64, "fp32": CASCADE_FP32_MIXED, "fp32_mixed": CASCADE_FP32_MIXED,
+                "fp32_fine": CASCADE_FP32_MIXED_FINE}[prec]
     return cascade_params(
         nx=int(p["nx"]), ppc=int(p["ppc"]), dx=float(p["dx"]), dt=float(p["dt"]),
         n0=float(p["n0"]), u_spread=float(p["u_spread"]), seed=int(p["seed"]),

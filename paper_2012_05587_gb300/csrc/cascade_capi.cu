@@ -57,7 +57,9 @@ int validate(const cascade_params* p) {
   else if (!(p->eps_gamma / p->gamma_thr < 2.0 / 3.0)) why = "f = eps_gamma / gamma_thr >= 2/3";
   else if (p->particle_cap < 1) why = "particle_cap < 1";
   else if (p->photon_cap < 0) why = "photon_cap < 0";
-  else if (p->precision != CASCADE_FP64 && p->precision != CASCADE_FP32_MIXED) why = "unknown precision";
+  else if (p->precision != CASCADE_FP64 && p->precision != CASCADE_FP32_MIXED &&
+           p->precision != CASCADE_FP32_MIXED_FINE)
+    why = "unknown precision";
   else if (p->diag_ring < 0) why = "diag_ring < 0";
   if (why) {
     snprintf(g_msg, sizeof(g_msg), "invalid parameters: %s", why);
@@ -188,6 +190,7 @@ int setup(const cascade_params* params, void* stream, cascade_t** out) {
   const double hh = 0.5 * params->eps_gamma;
   d.u_pair = sqrt(hh * hh - 1.0);
   d.ring_n = pl.ring;
+  d.fine_deposit = params->precision == CASCADE_FP32_MIXED_FINE ? 1 : 0;
   e = params->precision == CASCADE_FP64 ? configure_fp64(d, h->num_sms) : configure_fp32(d, h->num_sms);
   if (e != cudaSuccess) return cuda_fail(e, "configure");
 

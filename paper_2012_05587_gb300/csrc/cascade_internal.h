@@ -60,6 +60,9 @@ struct Dev {
   int block_push;      // threads per CTA of the particle kernel
   int grid_field;      // CTAs of the field kernel
   int variant;         // particle-kernel variant, see PushVariant
+  int push_dep;        // current accumulator, see AccOf in cascade_kernels.cuh
+  int push_fast;       // 1: gamma from one reciprocal square root (FP32 only)
+  int fine_deposit;    // FP32: two-word accumulator (CASCADE_FP32_MIXED_FINE)
   long long min_per_cta;  // particles per active CTA before another CTA is woken
 };
 

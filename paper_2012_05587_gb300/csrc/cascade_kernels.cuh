@@ -16,6 +16,7 @@
 
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "cascade_internal.h"
 
@@ -163,11 +164,61 @@ __device__ __forceinline__ void st4(double* p, const double v[4]) {
 }
 
 // ---------------------------------------------------------------------------
-// The particle kernel.  Variant V: see PushVariant.  Acc is the type of the
-// per-CTA shared-memory current accumulator (the precision of the particles).
+// gamma and velocity.  Exact: gamma = sqrt(1 + u^2) and v = u / gamma rounded
+// as written (the plain definition).  Fast (FP32 only): one reciprocal square
+// root, r = 1/sqrt(1 + u^2), gamma = (1 + u^2) r, v = u r.
 // ---------------------------------------------------------------------------
-template <class Real, class Acc, int V>
+template <class Real, bool FAST>
+struct Kin {
+  __device__ static __forceinline__ void eval(Real u, Real dtdx, Real& g, Real& dd) {
+    g = sqrt(Real(1) + u * u);
+    dd = u / g * dtdx;
+  }
+};
+template <>
+struct Kin<float, true> {
+  __device__ static __forceinline__ void eval(float u, float dtdx, float& g, float& dd) {
+    const float a = 1.0f + u * u;
+    const float r = rsqrtf(a);
+    g = a * r;
+    dd = (u * r) * dtdx;
+  }
+};
+
+// Per-CTA current accumulator in shared memory, one entry per edge:
+//   DEP 0  Real atomics (FP64 mode; shared-memory FP32 atomic adds measured
+//          1.6x slower than integer ones on this part)
+//   DEP 1  int32 fixed point at 2^-k.  Every contribution is below dt/dx in
+//          magnitude and a CTA handles at most P particles in a launch, so k
+//          = floor(log2(2^30 / (P dt/dx))) keeps every sum below 2^30: no
+//          overflow is possible.  Rounding to nearest, unbiased, error at most
+//          2^-(k+1) per contribution.
+//   DEP 4  two int32 words: the DEP 1 word plus a second word holding the
+//          rounding residual of the first at a finer scale; the residual is at
+//          most half a coarse step, so that sum cannot overflow either.
+//          Resolution about 2^-20, one more atomic per contribution.
+template <class Real, int DEP>
+struct AccOf {
+  typedef Real type;
+};
+template <class Real>
+struct AccOf<Real, 1> {
+  typedef int type;
+};
+template <class Real>
+struct AccOf<Real, 4> {
+  typedef int type;
+};
+
+// ---------------------------------------------------------------------------
+// The particle kernel.  V: where E and the current accumulator live (see
+// PushVariant).  Four particles per thread and iteration: their eight E
+// loads are issued together, then the push/move of all four, then the
+// deposits, then (only if a lane crossed gamma_thr) the emissions.
+// ---------------------------------------------------------------------------
+template <class Real, int V, int DEP, bool FAST>
 __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
+  typedef typename AccOf<Real, DEP>::type Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   Ctl* ctl = d.ctl;
@@ -175,13 +226,18 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
   if ((int)blockIdx.x >= G) return;
 
   const int nx = d.nx;
+  const size_t eb = ((size_t)nx * sizeof(Real) + 15) & ~size_t(15);
   Real* Es = reinterpret_cast<Real*>(smem_raw);
-  Acc* Ss = reinterpret_cast<Acc*>(smem_raw + ((nx * sizeof(Real) + 15) & ~size_t(15)));
+  Acc* Ss = reinterpret_cast<Acc*>(smem_raw + eb);
+  int* Ls = reinterpret_cast<int*>(smem_raw + 2 * eb);  // DEP 4 fine word
   if (V != kGlobEGlobS) {
     for (int i = threadIdx.x; i < nx; i += blockDim.x) Es[i] = (Real)d.E[i];
   }
   if (V == kSmemESmemS) {
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) Ss[i] = Acc(0);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      Ss[i] = Acc(0);
+      if (DEP == 4) Ls[i] = 0;
+    }
   }
   __syncthreads();
 
@@ -191,18 +247,43 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
   const long long ph_tail = ctl->ph_tail;
   const long long room = d.ph_cap - (ph_tail - ctl->conv_end);
   const long long ph_mask = d.ph_cap - 1;
+  const long long stride = (long long)G * blockDim.x;
 
   const Real dt = (Real)d.dt, dtdx = (Real)d.dtdx;
   const Real thr = (Real)d.gamma_thr, eps = (Real)d.eps_gamma, lpf = (Real)d.lpp_frac;
   const Real one = Real(1), half = Real(0.5), zero = Real(0);
   Real* ph_off = static_cast<Real*>(d.ph_off);
 
+  // fixed-point scale: every contribution is below dtdx in magnitude and this
+  // CTA handles at most iters * blockDim * 4 particles, so the sum of any
+  // edge stays below 2^30
+  float fx_scale = 1.0f, fx_inv = 1.0f, lo_scale = 1.0f, lo_inv = 1.0f;
+  if (DEP == 1 || DEP == 4) {
+    const long long iters = (C + stride - 1) / stride;
+    const double pcta = (double)(iters * blockDim.x * 4) + 1.0;
+    int k = (int)floor(log2(1073741824.0 / (pcta * d.dtdx + 1.0)));
+    k = k < 0 ? 0 : (k > 30 ? 30 : k);
+    fx_scale = ldexpf(1.0f, k);
+    fx_inv = ldexpf(1.0f, -k);
+    if (DEP == 4) {
+      // residuals are at most 2^-(k+1): pcta of them stay below 2^30 at 2^(k+1+m)
+      int m = (int)floor(log2(1073741824.0 / pcta));
+      m = m < 0 ? 0 : m;
+      int kl = k + 1 + m;
+      kl = kl > 60 ? 60 : kl;
+      lo_scale = ldexpf(1.0f, kl);
+      lo_inv = ldexpf(1.0f, -kl);
+    }
+  }
+
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const long long stride = (long long)G * blockDim.x;
   double gsum_total = 0.0;
 
-  for (long long wb = (long long)blockIdx.x * blockDim.x + warp * 32; wb < C; wb += stride) {
+  const long long first_wb = (long long)blockIdx.x * blockDim.x;
+  const long long iters_cta = (C > first_wb) ? (C - first_wb + stride - 1) / stride : 0;
+  for (long long it = 0; it < iters_cta; ++it) {
+    const long long wb = first_wb + it * stride + warp * 32;
     const long long ch = wb + lane;
     int s = 0, cnt = 0;
     long long base = 0;
@@ -233,81 +314,124 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
     }
     const Real q = s ? one : -one;
     const Real qdt = s ? dt : -dt;
-    Real gsum = zero;
+
+    // gather: linear between the two edges bracketing each particle
+    Real Ep[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const bool valid = j < cnt;
-      int k = 0;
-      int enc = 0;
-      Real oc = zero;
-      if (valid) {
-        const int c = cl[j];
-        const Real o = of[j];
-        // gather: linear between the two edges bracketing the particle
-        int ia, ib;
-        Real w;
-        if (o >= half) {
-          ia = c;
-          ib = (c + 1 == nx) ? 0 : c + 1;
-          w = o - half;
-        } else {
-          ia = (c == 0) ? nx - 1 : c - 1;
-          ib = c;
-          w = o + half;
-        }
-        Real Ea, Eb;
-        if (V == kGlobEGlobS) {
-          Ea = (Real)__ldg(d.E + ia);
-          Eb = (Real)__ldg(d.E + ib);
-        } else {
-          Ea = Es[ia];
-          Eb = Es[ib];
-        }
-        const Real Ep = (one - w) * Ea + w * Eb;
-        // push: du/dt = q E
-        Real u = uu[j] + qdt * Ep;
-        Real g = sqrt(one + u * u);
-        // move: dx/dt = u / gamma, in cell units
-        const Real dd = u / g * dtdx;
-        Real o2 = o + dd;
-        int c2 = c;
-        // charge-conserving deposit: q * (offset change) per edge crossed
-        Acc a1, a2 = Acc(0);
-        int e2 = -1;
+      const int c = cl[j];
+      const Real o = of[j];
+      const bool hi = o >= half;
+      const int ia = hi ? c : ((c == 0) ? nx - 1 : c - 1);
+      const int ib = hi ? ((c + 1 == nx) ? 0 : c + 1) : c;
+      const Real w = hi ? o - half : o + half;
+      Real Ea, Eb;
+      if (V == kGlobEGlobS) {
+        Ea = (Real)__ldg(d.E + ia);
+        Eb = (Real)__ldg(d.E + ib);
+      } else {
+        Ea = Es[ia];
+        Eb = Es[ib];
+      }
+      Ep[j] = (one - w) * Ea + w * Eb;
+    }
+
+    // push (du/dt = q E), move (dx/dt = u / gamma, cell units) and the
+    // charge-conserving current: q * (offset change) per edge crossed
+    Real g[4], a1[4], a2[4];
+    int e1[4], e2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = cl[j];
+      const Real o = of[j];
+      const Real u = uu[j] + qdt * Ep[j];
+      Real gj, dd;
+      Kin<Real, FAST>::eval(u, dtdx, gj, dd);
+      Real o2 = o + dd;
+      int c2 = c;
+      Real b1, b2 = zero;
+      int f2 = -1;
+      if (o2 >= one) {
+        b1 = q * (one - o);
+        c2 = (c + 1 == nx) ? 0 : c + 1;
+        o2 = o2 - one;
+        f2 = c2;
+        b2 = q * o2;
+      } else if (o2 < zero) {
+        b1 = q * (zero - o);
+        c2 = (c == 0) ? nx - 1 : c - 1;
+        o2 = o2 + one;
+        f2 = c2;
+        b2 = q * (o2 - one);
         if (o2 >= one) {
-          a1 = (Acc)(q * (one - o));
-          c2 = (c + 1 == nx) ? 0 : c + 1;
-          o2 = o2 - one;
-          e2 = c2;
-          a2 = (Acc)(q * o2);
-        } else if (o2 < zero) {
-          a1 = (Acc)(q * (zero - o));
-          c2 = (c == 0) ? nx - 1 : c - 1;
-          o2 = o2 + one;
-          e2 = c2;
-          a2 = (Acc)(q * (o2 - one));
-          if (o2 >= one) {
-            o2 = zero;
-            c2 = c;
+          o2 = zero;
+          c2 = c;
+        }
+      } else {
+        b1 = q * (o2 - o);
+      }
+      const bool valid = j < cnt;
+      e1[j] = valid ? c : -1;
+      e2[j] = valid ? f2 : -1;
+      a1[j] = b1;
+      a2[j] = b2;
+      g[j] = valid ? gj : one;
+      cl[j] = c2;
+      of[j] = o2;
+      uu[j] = u;
+    }
+
+    // deposit
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (V == kSmemESmemS) {
+        if (DEP == 1) {
+          if (e1[j] >= 0) atomicAdd(&Ss[e1[j]], __float2int_rn((float)a1[j] * fx_scale));
+          if (e2[j] >= 0) atomicAdd(&Ss[e2[j]], __float2int_rn((float)a2[j] * fx_scale));
+        } else if (DEP == 4) {
+          if (e1[j] >= 0) {
+            const float a = (float)a1[j];
+            const int qh = __float2int_rn(a * fx_scale);
+            const int ql = __float2int_rn((a - (float)qh * fx_inv) * lo_scale);  // residual is exact
+            atomicAdd(&Ss[e1[j]], qh);
+            if (ql != 0) atomicAdd(&Ls[e1[j]], ql);
+          }
+          if (e2[j] >= 0) {
+            const float a = (float)a2[j];
+            const int qh = __float2int_rn(a * fx_scale);
+            const int ql = __float2int_rn((a - (float)qh * fx_inv) * lo_scale);
+            atomicAdd(&Ss[e2[j]], qh);
+            if (ql != 0) atomicAdd(&Ls[e2[j]], ql);
           }
         } else {
-          a1 = (Acc)(q * (o2 - o));
+          if (e1[j] >= 0) atomicAdd(&Ss[e1[j]], (Acc)a1[j]);
+          if (e2[j] >= 0) atomicAdd(&Ss[e2[j]], (Acc)a2[j]);
         }
-        if (V == kSmemESmemS) {
-          atomicAdd(&Ss[c], a1);
-          if (e2 >= 0) atomicAdd(&Ss[e2], a2);
-        } else {
-          atomicAdd(&d.S_glob[c], (double)a1);
-          if (e2 >= 0) atomicAdd(&d.S_glob[e2], (double)a2);
-        }
-        // QED (Section 2): threshold emission with recoil
+      } else {
+        if (e1[j] >= 0) atomicAdd(&d.S_glob[e1[j]], (double)a1[j]);
+        if (e2[j] >= 0) atomicAdd(&d.S_glob[e2[j]], (double)a2[j]);
+      }
+    }
+
+    // QED (Section 2): threshold emission with recoil; photons appended with
+    // one warp-wide scan and one global atomic per slot that has emitters
+    const bool hot = (g[0] >= thr) | (g[1] >= thr) | (g[2] >= thr) | (g[3] >= thr) |
+                     !(g[0] <= Real(1e30)) | !(g[1] <= Real(1e30)) | !(g[2] <= Real(1e30)) |
+                     !(g[3] <= Real(1e30));
+    if (__any_sync(kFull, hot)) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int k = 0;
+        int enc = 0;
+        Real oc = zero;
+        Real u = uu[j], gj = g[j];
         bool emit;
         const bool fwd = u > zero;  // direction kept through the recoil
-        if (!(g <= Real(1e30))) {
-          // non-finite or absurd gamma: the run has blown up; flag it and do not emit
+        if (!(gj <= Real(1e30))) {
+          // non-finite or absurd gamma: the run has blown up; flag it, no emission
           set_error(ctl, CASCADE_ERR_NONFINITE);
           emit = false;
-        } else if (sizeof(Real) == 4 && g > Real(1e6)) {
+        } else if (sizeof(Real) == 4 && gj > Real(1e6)) {
           // large gamma: threshold test and recoil in FP64
           const double ud = (double)u;
           const double gd = sqrt(1.0 + ud * ud);
@@ -316,20 +440,22 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
             k = 1 + (int)fmin(floor((gd - d.gamma_thr) / d.eps_gamma), (double)kMaxPhotonsPerStep);
             const double g2 = gd - (double)k * d.eps_gamma;
             u = (Real)((fwd ? 1.0 : -1.0) * sqrt(g2 * g2 - 1.0));
-            g = (Real)g2;
+            gj = (Real)g2;
           }
         } else {
-          emit = g >= thr;
+          emit = gj >= thr;
           if (emit) {
-            k = 1 + (int)fmin(floor((g - thr) / eps), (Real)kMaxPhotonsPerStep);
-            const Real g2 = g - (Real)k * eps;
+            k = 1 + (int)fmin(floor((gj - thr) / eps), (Real)kMaxPhotonsPerStep);
+            const Real g2 = gj - (Real)k * eps;
             const Real sg = fwd ? one : -one;
             u = sg * sqrt(g2 * g2 - one);
-            g = g2;
+            gj = g2;
           }
         }
         if (emit) {
           // conversion point x + dir * l_pp, wrapped
+          const Real o2 = of[j];
+          const int c2 = cl[j];
           long long ci;
           if (fwd) {
             oc = o2 + lpf;
@@ -354,39 +480,37 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
           if (m < 0) m += nx;
           enc = (int)m | (fwd ? 0 : (int)0x80000000);
           if (k > 1) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->emit_multi), 1ull);
+          uu[j] = u;
+          g[j] = gj;
         }
-        cl[j] = c2;
-        of[j] = o2;
-        uu[j] = u;
-        gsum += g;
-      }
-      // warp-aggregated append of this slot's photons
-      const unsigned em = __ballot_sync(kFull, k > 0);
-      if (em) {
-        unsigned long long kk = (unsigned long long)k;
-        unsigned long long incl = kk;
+        const unsigned em = __ballot_sync(kFull, k > 0);
+        if (em) {
+          const unsigned long long kk = (unsigned long long)k;
+          unsigned long long incl = kk;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const unsigned long long v = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += v;
-        }
-        const unsigned long long tot = __shfl_sync(kFull, incl, 31);
-        unsigned long long b0 = 0;
-        if (lane == 0) b0 = atomicAdd(&ctl->emit_count, tot);
-        b0 = __shfl_sync(kFull, b0, 0);
-        const unsigned long long first = b0 + incl - kk;
-        for (int m = 0; m < k; ++m) {
-          const unsigned long long pos = first + m;
-          if ((long long)pos < room) {
-            const long long slot = (ph_tail + (long long)pos) & ph_mask;
-            d.ph_cell[slot] = enc;
-            ph_off[slot] = oc;
-          } else {
-            set_error(ctl, CASCADE_ERR_PHOTON_CAPACITY);
+          for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+          }
+          const unsigned long long tot = __shfl_sync(kFull, incl, 31);
+          unsigned long long b0 = 0;
+          if (lane == 0) b0 = atomicAdd(&ctl->emit_count, tot);
+          b0 = __shfl_sync(kFull, b0, 0);
+          const unsigned long long first = b0 + incl - kk;
+          for (int m = 0; m < k; ++m) {
+            const unsigned long long pos = first + m;
+            if ((long long)pos < room) {
+              const long long slot = (ph_tail + (long long)pos) & ph_mask;
+              d.ph_cell[slot] = enc;
+              ph_off[slot] = oc;
+            } else {
+              set_error(ctl, CASCADE_ERR_PHOTON_CAPACITY);
+            }
           }
         }
       }
     }
+
     if (cnt == 4) {
       st4(cellp, cl);
       st4(offp, of);
@@ -401,7 +525,10 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
         }
       }
     }
-    gsum_total += (double)gsum;
+    Real gs = zero;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gs += (j < cnt) ? g[j] : zero;
+    gsum_total += (double)gs;
   }
 
   // sum of gamma over the CTA (FP64)
@@ -416,8 +543,12 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
     if (lane == 0) d.uk_part[blockIdx.x] = v;
   }
   if (V == kSmemESmemS) {
-    Acc* P = static_cast<Acc*>(d.S_part) + (size_t)blockIdx.x * d.nxp;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) P[i] = Ss[i];
+    Real* P = static_cast<Real*>(d.S_part) + (size_t)blockIdx.x * d.nxp;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      if (DEP == 1) P[i] = (Real)((float)Ss[i] * fx_inv);
+      else if (DEP == 4) P[i] = (Real)((double)Ss[i] * (double)fx_inv + (double)Ls[i] * (double)lo_inv);
+      else P[i] = (Real)Ss[i];
+    }
   }
 }
 
@@ -596,29 +727,68 @@ __global__ void k_gauss_reduce(Dev d, const double* rho_dx, double* out) {
 // ---------------------------------------------------------------------------
 // Launchers (instantiated per precision by the including .cu file).
 // ---------------------------------------------------------------------------
-template <class Real, class Acc>
+// Particle-kernel variants compiled for one precision: (V, DEP, FAST).  FP64
+// keeps only the exact variants; FP32 adds the fast gamma and the fixed-point
+// accumulator.
+template <class Real>
+struct PushTable {
+  static const void* get(int V, int dep, bool fast);
+};
+template <>
+inline const void* PushTable<double>::get(int V, int, bool) {
+  if (V == kSmemESmemS) return reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false>);
+  if (V == kSmemEGlobS) return reinterpret_cast<const void*>(&k_push<double, kSmemEGlobS, 0, false>);
+  return reinterpret_cast<const void*>(&k_push<double, kGlobEGlobS, 0, false>);
+}
+template <>
+inline const void* PushTable<float>::get(int V, int dep, bool) {
+  if (V == kSmemESmemS) {
+    if (dep == 4) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 4, true>);
+    return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true>);
+  }
+  if (V == kSmemEGlobS) return reinterpret_cast<const void*>(&k_push<float, kSmemEGlobS, 0, true>);
+  return reinterpret_cast<const void*>(&k_push<float, kGlobEGlobS, 0, true>);
+}
+
+inline int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return (v && *v) ? atoi(v) : dflt;
+}
+
+template <class Real>
 struct Launchers {
-  static size_t smem_bytes(int nx, int variant) {
+  // E (Real) plus the accumulator: one Real or int32 word per edge, two
+  // int32 words for DEP 4.
+  static size_t smem_bytes(int nx, int variant, int dep = 0) {
     const size_t eb = ((size_t)nx * sizeof(Real) + 15) & ~size_t(15);
-    const size_t sb = ((size_t)nx * sizeof(Acc) + 15) & ~size_t(15);
-    if (variant == kSmemESmemS) return eb + sb;
+    if (variant == kSmemESmemS) return (dep == 4 ? 3 : 2) * eb;
     if (variant == kSmemEGlobS) return eb;
     return 0;
   }
 
-  static const void* push_fn(int variant) {
-    if (variant == kSmemESmemS) return reinterpret_cast<const void*>(&k_push<Real, Acc, kSmemESmemS>);
-    if (variant == kSmemEGlobS) return reinterpret_cast<const void*>(&k_push<Real, Acc, kSmemEGlobS>);
-    return reinterpret_cast<const void*>(&k_push<Real, Acc, kGlobEGlobS>);
-  }
+  static const void* push_fn(const Dev& d) { return PushTable<Real>::get(d.variant, d.push_dep, d.push_fast != 0); }
 
   static cudaError_t configure(Dev& d, int num_sms) {
     const size_t limit = 200 * 1024;
+    int dep = 0, fast = 0;
+    if (sizeof(Real) == 4) {
+      dep = d.fine_deposit ? 4 : 1;
+      const int forced = env_int("CASCADE_PUSH_DEP", 0);  // measurement override: 1 or 4
+      if (forced == 1 || forced == 4) dep = forced;
+      fast = 1;
+    }
     int variant = kGlobEGlobS;
-    if (smem_bytes(d.nx, kSmemESmemS) <= limit) variant = kSmemESmemS;
-    else if (smem_bytes(d.nx, kSmemEGlobS) <= limit) variant = kSmemEGlobS;
-    const size_t smem = smem_bytes(d.nx, variant);
-    const void* fn = push_fn(variant);
+    if (smem_bytes(d.nx, kSmemESmemS, dep) <= limit) variant = kSmemESmemS;
+    else if (dep == 4 && smem_bytes(d.nx, kSmemESmemS, 1) <= limit) {
+      dep = 1;  // the two-word accumulator does not fit: one word
+      variant = kSmemESmemS;
+    } else if (smem_bytes(d.nx, kSmemEGlobS) <= limit) variant = kSmemEGlobS;
+    if (variant != kSmemESmemS) dep = 0;
+    d.variant = variant;
+    d.push_dep = dep;
+    d.push_fast = fast;
+    const size_t smem = smem_bytes(d.nx, variant, dep);
+    const void* fn = push_fn(d);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int block = 1024;
@@ -626,7 +796,6 @@ struct Launchers {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    d.variant = variant;
     d.block_push = block;
     d.grid_push = per_sm * num_sms;
     d.grid_field = (d.nx + kFieldBlock - 1) / kFieldBlock;
@@ -649,20 +818,17 @@ struct Launchers {
   static cudaError_t step(const Dev& d, cudaStream_t st, cudaEvent_t before = nullptr,
                           cudaEvent_t after = nullptr) {
     k_convert<Real><<<d.grid_push, 256, 0, st>>>(d);
-    const size_t smem = smem_bytes(d.nx, d.variant);
     if (before) cudaEventRecord(before, st);
-    if (d.variant == kSmemESmemS) {
-      k_push<Real, Acc, kSmemESmemS><<<d.grid_push, d.block_push, smem, st>>>(d);
-    } else if (d.variant == kSmemEGlobS) {
-      k_push<Real, Acc, kSmemEGlobS><<<d.grid_push, d.block_push, smem, st>>>(d);
-    } else {
-      k_push<Real, Acc, kGlobEGlobS><<<d.grid_push, d.block_push, 0, st>>>(d);
-    }
+    Dev arg = d;
+    void* args[] = {&arg};
+    cudaError_t e = cudaLaunchKernel(push_fn(d), dim3(d.grid_push), dim3(d.block_push), args,
+                                     smem_bytes(d.nx, d.variant, d.push_dep), st);
+    if (e != cudaSuccess) return e;
     if (after) cudaEventRecord(after, st);
     if (d.variant == kSmemESmemS) {
-      k_field<Acc, true><<<d.grid_field, kFieldBlock, 0, st>>>(d);
+      k_field<Real, true><<<d.grid_field, kFieldBlock, 0, st>>>(d);
     } else {
-      k_field<Acc, false><<<d.grid_field, kFieldBlock, 0, st>>>(d);
+      k_field<Real, false><<<d.grid_field, kFieldBlock, 0, st>>>(d);
     }
     return cudaGetLastError();
   }
@@ -678,19 +844,19 @@ struct Launchers {
 
 }  // namespace cpic
 
-#define CASCADE_DEFINE_LAUNCHERS(SUFFIX, REAL, ACC)                                               \
+#define CASCADE_DEFINE_LAUNCHERS(SUFFIX, REAL)                                               \
   namespace cpic {                                                                             \
   cudaError_t seed_##SUFFIX(const Dev& d, long long npairs, int ppc, unsigned long long seed,    \
                             double u_spread, cudaStream_t s) {                                    \
-    return Launchers<REAL, ACC>::seed(d, npairs, ppc, seed, u_spread, s);                         \
+    return Launchers<REAL>::seed(d, npairs, ppc, seed, u_spread, s);                         \
   }                                                                                               \
-  cudaError_t step_##SUFFIX(const Dev& d, cudaStream_t s) { return Launchers<REAL, ACC>::step(d, s); } \
+  cudaError_t step_##SUFFIX(const Dev& d, cudaStream_t s) { return Launchers<REAL>::step(d, s); } \
   cudaError_t step_timed_##SUFFIX(const Dev& d, cudaStream_t s, cudaEvent_t b, cudaEvent_t a) {  \
-    return Launchers<REAL, ACC>::step(d, s, b, a);                                                \
+    return Launchers<REAL>::step(d, s, b, a);                                                \
   }                                                                                               \
   cudaError_t gauss_##SUFFIX(const Dev& d, double* rho_dx, double* out, cudaStream_t s) {         \
-    return Launchers<REAL, ACC>::gauss(d, rho_dx, out, s);                                        \
+    return Launchers<REAL>::gauss(d, rho_dx, out, s);                                        \
   }                                                                                               \
-  cudaError_t configure_##SUFFIX(Dev& d, int num_sms) { return Launchers<REAL, ACC>::configure(d, num_sms); } \
-  size_t partial_bytes_##SUFFIX() { return sizeof(ACC); }                                         \
+  cudaError_t configure_##SUFFIX(Dev& d, int num_sms) { return Launchers<REAL>::configure(d, num_sms); } \
+  size_t partial_bytes_##SUFFIX() { return sizeof(REAL); }                                         \
   }

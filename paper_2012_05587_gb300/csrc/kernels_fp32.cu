@@ -4,4 +4,4 @@
 // threshold test of leptons above gamma = 1e6.
 #include "cascade_kernels.cuh"
 
-CASCADE_DEFINE_LAUNCHERS(fp32, float, float)
+CASCADE_DEFINE_LAUNCHERS(fp32, float)

@@ -3,4 +3,4 @@
 // double-precision definition of the method.
 #include "cascade_kernels.cuh"
 
-CASCADE_DEFINE_LAUNCHERS(fp64, double, double)
+CASCADE_DEFINE_LAUNCHERS(fp64, double)

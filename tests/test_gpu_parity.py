@@ -179,14 +179,15 @@ def _ensemble(d, E_first_zero_window=200):
     }
 
 
-def test_fp32_mixed_ensemble_small_cascade():
+@pytest.mark.parametrize("precision", ["fp32", "fp32_fine"])
+def test_fp32_mixed_ensemble_small_cascade(precision):
     """FP32-mixed vs the FP64 oracle on ensemble diagnostics (2%): final pair
     count, screening time, peak field after screening, oscillation period,
     final energy -- averaged over seeds."""
     keys = ("pairs", "peak_after_screen", "period", "energy", "first_zero")
     g_all, r_all = [], []
     for run in range(4):
-        p = W.small_cascade(run=run, precision="fp32")
+        p = W.small_cascade(run=run, precision=precision)
         d_ref = oracle.Oracle(oracle_params(p)).step(p["steps"])
         with Cascade(p) as c:
             c.step(p["steps"])
@@ -201,7 +202,7 @@ def test_fp32_mixed_ensemble_small_cascade():
 
 # --- full-size configuration: first steps against the oracle -------------------------------
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-5), ("fp32", 2e-4)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-5), ("fp32", 2e-4), ("fp32_fine", 2e-4)])
 def test_large_cascade_first_steps(precision, tol):
     """Nx = 16384, 64 + 64 per cell: the launch configuration of the benchmark.
     60 steps include the first emissions (t_a = 0.5 = 20 steps) and the first
@@ -262,3 +263,22 @@ def test_species_counts_and_pair_bookkeeping():
         seed = p["nx"] * p["ppc"]
         assert np.array_equal(d["n_elec"], d["n_posi"])
         assert np.array_equal(d["n_elec"], seed + d["n_pairs_total"])
+
+
+def test_fine_deposit_is_closer_to_fp64():
+    """The two-word accumulator tracks the FP64 current more closely than the
+    one-word one on the same full-size state (first 30 steps, before any
+    emission, so both runs see the same particles)."""
+    errs = {}
+    p0 = W.large_cascade()
+    p0["particle_cap"] = 1 << 22
+    ref = oracle.Oracle(oracle_params(p0))
+    ref.step(30)
+    _, J_ref = ref.fields()
+    for prec in ("fp32", "fp32_fine"):
+        with Cascade(dict(p0, precision=prec)) as c:
+            c.step(30)
+            _, J = c.fields()
+        errs[prec] = np.abs(J - J_ref).max() / np.abs(J_ref).max()
+    assert errs["fp32_fine"] <= errs["fp32"]
+    assert errs["fp32_fine"] < 1e-5
