@@ -178,6 +178,42 @@ int cascade_set_timing(cascade_t* h, int32_t enable);
 int cascade_timing(cascade_t* h, double* particle_kernel_ms, int64_t* particle_kernel_launches,
                    int64_t* kernels_launched);
 
+/* Largest grid cascade_gauss_noalloc accepts. */
+#define CASCADE_NOALLOC_MAX_NX 65536
+
+/* Gauss's-law residual max_i |E_{i+1/2} - E_{i-1/2} - dx rho_i| of a state
+ * held by the caller, computed without allocating any memory.  The paper has
+ * no counterpart: this is a library service, the same check as cascade_gauss
+ * but on the caller's buffers.  It exists for callers that cannot allocate
+ * device memory: applications that reserve all device memory for their own
+ * pool at start-up and forbid libraries to allocate, plug-ins whose host
+ * program owns every allocation, and real-time loops where cudaMalloc (which
+ * may synchronise the whole device) is not allowed.  Its scratch (charge per
+ * node and the result: CASCADE_NOALLOC_MAX_NX + 32 doubles, 512.25 KiB) is a
+ * static device array that every GPU which loads this library holds until
+ * the process exits.
+ *   nx          cells, 2 .. CASCADE_NOALLOC_MAX_NX (otherwise
+ *               CASCADE_ERR_INVALID_ARG, with a message naming the limit)
+ *   dx          cell size (the residual is in units of E)
+ *   w           macro-particle weight n0 dx / ppc
+ *   precision   CASCADE_FP64: offsets are double; otherwise float
+ *   n_elec, cell_e, off_e / n_posi, cell_p, off_p
+ *               particle counts and DEVICE arrays (cell int32 in [0, nx),
+ *               offset in [0, 1)), read only
+ *   E           DEVICE array of nx doubles, E_{i+1/2} at [i], read only
+ *   resid_out   HOST double receiving the residual
+ *   cuda_stream stream the work is issued on; the call synchronises it
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the one array and clears it first: calls that
+ * overlap on the GPU (other streams or threads at the same time) race on it,
+ * so serialise them.  No cudaMalloc, cudaFree or allocating library call is
+ * made. */
+int cascade_gauss_noalloc(int32_t nx, double dx, double w, int32_t precision,
+                          int64_t n_elec, const int32_t* cell_e, const void* off_e,
+                          int64_t n_posi, const int32_t* cell_p, const void* off_p,
+                          const double* E, double* resid_out, void* cuda_stream);
+
 /* Release all device memory of the handle (NULL is accepted). */
 int cascade_destroy(cascade_t* h);
 

@@ -25,6 +25,7 @@ UNITS = {
     "cascade_capi.cu": [],
     "kernels_fp64.cu": ["-fmad=false"],
     "kernels_fp32.cu": [],
+    "cascade_noalloc.cu": [],
 }
 
 

@@ -101,6 +101,8 @@ def load() -> ctypes.CDLL:
             "cascade_footprint": ([P(cascade_params), P(i32), P(ctypes.c_size_t)], ctypes.c_int),
             "cascade_set_timing": ([vp, i32], ctypes.c_int),
             "cascade_timing": ([vp, P(f64), P(i64), P(i64)], ctypes.c_int),
+            "cascade_gauss_noalloc": ([i32, f64, f64, i32, i64, vp, vp, i64, vp, vp, vp, P(f64), vp],
+                                      ctypes.c_int),
             "cascade_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "cascade_last_error_message": ([], ctypes.c_char_p),
         }
@@ -259,6 +261,18 @@ def cascade_timing(h) -> dict:
     k = ctypes.c_int64()
     check("cascade_timing", load().cascade_timing(h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)))
     return {"particle_kernel_ms": ms.value, "particle_kernel_launches": n.value, "kernels_launched": k.value}
+
+
+def cascade_gauss_noalloc(nx: int, dx: float, w: float, precision: int, n_elec: int, cell_e: int, off_e: int,
+                          n_posi: int, cell_p: int, off_p: int, E: int, stream: int = 0) -> float:
+    """Gauss residual of caller-held DEVICE buffers (pointers as ints); the
+    library allocates nothing for this call."""
+    r = ctypes.c_double()
+    check("cascade_gauss_noalloc", load().cascade_gauss_noalloc(
+        int(nx), float(dx), float(w), int(precision), int(n_elec), ctypes.c_void_p(cell_e),
+        ctypes.c_void_p(off_e), int(n_posi), ctypes.c_void_p(cell_p), ctypes.c_void_p(off_p),
+        ctypes.c_void_p(E), ctypes.byref(r), ctypes.c_void_p(stream)))
+    return r.value
 
 
 def cascade_footprint(params: dict):

@@ -552,3 +552,11 @@ const char* cascade_status_string(int status) {
 const char* cascade_last_error_message(void) { return g_msg; }
 
 }  // extern "C"
+
+namespace cpic {
+void set_error_message(const char* msg) { snprintf(g_msg, sizeof(g_msg), "%s", msg); }
+}  // namespace cpic
+
+extern "C" {
+
+}  // extern "C"

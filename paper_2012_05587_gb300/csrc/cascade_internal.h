@@ -74,6 +74,9 @@ enum PushVariant {
 
 constexpr int kFieldBlock = 256;
 
+// Record the detail of a failure for cascade_last_error_message (calling thread).
+void set_error_message(const char* msg);
+
 // Kernel launchers, one set per precision (defined in kernels_fp64.cu and
 // kernels_fp32.cu).  They return a cudaError_t.
 #define CASCADE_DECLARE_LAUNCHERS(SUFFIX)                                                       \
