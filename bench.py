@@ -38,6 +38,11 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s incl. deposit+QED (batched FP32 vs plain FP64), % HBM roofline; p50/p99"
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = {"fp32": 24, "fp64": 40}
+# DRAM bytes (read + write) per particle-step of the FP32 particle kernel, from
+# one ncu capture of this kernel on a smaller post-screening case of the same
+# grid (profiles/k_push_fp32_post_screening.md: 785.0 MB for 3.487e7
+# particle-steps); traffic grows in proportion to the particles processed.
+MEASURED_DRAM_BYTES_PER_PARTICLE_STEP = {"fp32": 22.52}
 
 
 def parse():
@@ -52,6 +57,15 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cap", type=int, default=0, help="particle cap per species (0 = the workload's)")
     ap.add_argument("--ppc", type=int, default=0, help="seed particles per cell per species (0 = the workload's)")
+    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "sweep"],
+                    help="large: one large cascade (default); batch: the 256-cascade parameter scan in one "
+                         "launch per step; serve: Poisson arrivals admitted by footprint; sweep: FP32 vs FP64 "
+                         "errors of the ensemble diagnostics")
+    ap.add_argument("--batch-n", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=3000)
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--fp64-sample", type=int, default=8, help="cascades run one at a time in FP64 for comparison")
     return ap.parse_args()
 
 
@@ -179,6 +193,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "large":
+        import bench_workloads
+
+        return bench_workloads.run(args)
 
     import torch
     import torch.distributed as dist
@@ -247,8 +265,11 @@ def main():
     bpp = BYTES_PER_PARTICLE_STEP[prec]
     avg_push_s = tim["particle_kernel_ms"] / 1e3 / max(tim["particle_kernel_launches"], 1)
     achieved = bpp * ps / args.steps / avg_push_s / 1e9
+    tb = MEASURED_DRAM_BYTES_PER_PARTICLE_STEP.get(prec)
+    traffic = tb * ps / args.steps if tb else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_push (gather/push/move/deposit/emission)",
+            "traffic": traffic, "traffic_source": "ncu capture of a smaller case scaled per particle-step"
+            if tb else None, "kernel": "k_push (gather/push/move/deposit/emission)",
             "bytes_per_particle_step": bpp, "peak_source": peak_kind}
 
     # end to end through the C ABI with host buffers

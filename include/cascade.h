@@ -178,6 +178,66 @@ int cascade_set_timing(cascade_t* h, int32_t enable);
 int cascade_timing(cascade_t* h, double* particle_kernel_ms, int64_t* particle_kernel_launches,
                    int64_t* kernels_launched);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent cascades (uneven grids and particle counts)
+ * advanced together.  One step is four launches for the whole batch: photon
+ * conversion of every member, a plan that cuts every member's particles into
+ * work items, one persistent particle kernel that hands the items out
+ * dynamically, and one field kernel with a CTA per member.  Steps are
+ * replayed from a captured CUDA graph.  Each member keeps its own step
+ * target; members that reach it stop.  All members share the batch's
+ * precision (CASCADE_FP64 or one of the FP32 modes) and nx <= max_nx.
+ * ------------------------------------------------------------------------- */
+typedef struct cascade_batch cascade_batch_t;
+
+/* Empty batch of max_slots slots.  hbm_budget caps the device bytes that
+ * admitted members may hold (0 = no cap); max_nx sizes the shared-memory
+ * stage of the particle kernel (members need nx <= max_nx). */
+int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max_nx, size_t hbm_budget,
+                               void* cuda_stream, cascade_batch_t** out);
+
+/* Batch of n members created from params[0..n-1] (all in the Section 3
+ * initial state); max_nx is the largest member grid; every member starts
+ * with zero steps to do. */
+int cascade_batch_create(const cascade_params* params, int32_t n, size_t hbm_budget, void* cuda_stream,
+                         cascade_batch_t** out);
+
+/* Admit one cascade into a free slot with nsteps steps to run.  Its device
+ * memory is allocated and seeded on a private stream, so admission does not
+ * wait for the steps already queued.  CASCADE_ERR_BUSY: no free slot, or its
+ * footprint (cascade_footprint) would exceed the budget. */
+int cascade_batch_admit(cascade_batch_t* b, const cascade_params* params, int32_t nsteps, int32_t* slot_out);
+
+/* Add nsteps_each[i] steps to member i (host array of max_slots entries;
+ * empty slots ignore theirs) and run until every member is done.  Async. */
+int cascade_batch_step(cascade_batch_t* b, const int32_t* nsteps_each);
+
+/* Run up to nsteps batch steps (members with nothing left are skipped).
+ * Async; queues a copy of the members' remaining step counts behind them. */
+int cascade_batch_run(cascade_batch_t* b, int32_t nsteps);
+
+/* Slots whose admitted run has finished and that were not reported before.
+ * wait = 0: report only what the newest completed run shows (no blocking);
+ * wait != 0: wait for all queued work first. */
+int cascade_batch_poll(cascade_batch_t* b, int32_t* done_slots, int32_t max, int32_t* n_out, int32_t wait);
+
+/* Per-step records of one member (as cascade_diag; waits for the batch). */
+int cascade_batch_diag(cascade_batch_t* b, int32_t slot, cascade_diag_t* host_out, int32_t max, int32_t* n_out,
+                       double* E_host, double* J_host);
+
+/* Counts of one member (as cascade_counts; waits for the batch). */
+int cascade_batch_counts(cascade_batch_t* b, int32_t slot, int64_t* n_elec, int64_t* n_posi, int64_t* n_photon,
+                         int64_t* step);
+
+/* Free a member's device memory and its slot (waits for the batch). */
+int cascade_batch_release(cascade_batch_t* b, int32_t slot);
+
+/* Number of slots, occupied slots and device bytes held by members. */
+int cascade_batch_info(cascade_batch_t* b, int32_t* slots, int32_t* occupied, size_t* bytes_in_use);
+
+/* Release everything (NULL is accepted). */
+int cascade_batch_destroy(cascade_batch_t* b);
+
 /* Largest grid cascade_gauss_noalloc accepts. */
 #define CASCADE_NOALLOC_MAX_NX 65536
 

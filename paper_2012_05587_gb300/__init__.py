@@ -9,4 +9,4 @@ from .capi import (  # noqa: F401
     cascade_create_from_state, cascade_destroy, cascade_diag, cascade_footprint, cascade_gauss,
     cascade_particles, cascade_step, cascade_sync, load, use_torch_allocator,
 )
-from .cascade import Cascade  # noqa: F401
+from .cascade import Cascade, CascadeBatch  # noqa: F401

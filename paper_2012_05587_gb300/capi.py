@@ -103,6 +103,17 @@ def load() -> ctypes.CDLL:
             "cascade_timing": ([vp, P(f64), P(i64), P(i64)], ctypes.c_int),
             "cascade_gauss_noalloc": ([i32, f64, f64, i32, i64, vp, vp, i64, vp, vp, vp, P(f64), vp],
                                       ctypes.c_int),
+            "cascade_batch_create_slots": ([i32, i32, i32, ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
+            "cascade_batch_create": ([P(cascade_params), i32, ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
+            "cascade_batch_admit": ([vp, P(cascade_params), i32, P(i32)], ctypes.c_int),
+            "cascade_batch_step": ([vp, vp], ctypes.c_int),
+            "cascade_batch_run": ([vp, i32], ctypes.c_int),
+            "cascade_batch_poll": ([vp, vp, i32, P(i32), i32], ctypes.c_int),
+            "cascade_batch_diag": ([vp, i32, vp, i32, P(i32), vp, vp], ctypes.c_int),
+            "cascade_batch_counts": ([vp, i32, P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
+            "cascade_batch_release": ([vp, i32], ctypes.c_int),
+            "cascade_batch_info": ([vp, P(i32), P(i32), P(ctypes.c_size_t)], ctypes.c_int),
+            "cascade_batch_destroy": ([vp], ctypes.c_int),
             "cascade_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "cascade_last_error_message": ([], ctypes.c_char_p),
         }
@@ -281,3 +292,88 @@ def cascade_footprint(params: dict):
     cp = make_params(params)
     check("cascade_footprint", load().cascade_footprint(ctypes.byref(cp), ctypes.byref(npp), ctypes.byref(b)))
     return npp.value, b.value
+
+
+# --- batches ---------------------------------------------------------------------------
+
+def _prec_code(prec) -> int:
+    if isinstance(prec, str):
+        return {"fp64": CASCADE_FP64, "fp32": CASCADE_FP32_MIXED, "fp32_mixed": CASCADE_FP32_MIXED,
+                "fp32_fine": CASCADE_FP32_MIXED_FINE}[prec]
+    return int(prec)
+
+
+def cascade_batch_create_slots(max_slots: int, precision, max_nx: int, hbm_budget: int = 0,
+                               stream: int = 0) -> ctypes.c_void_p:
+    b = ctypes.c_void_p()
+    check("cascade_batch_create_slots", load().cascade_batch_create_slots(
+        int(max_slots), _prec_code(precision), int(max_nx), int(hbm_budget), ctypes.c_void_p(stream),
+        ctypes.byref(b)))
+    return b
+
+
+def cascade_batch_create(params: list, hbm_budget: int = 0, stream: int = 0) -> ctypes.c_void_p:
+    arr = (cascade_params * len(params))(*[make_params(p) for p in params])
+    b = ctypes.c_void_p()
+    check("cascade_batch_create", load().cascade_batch_create(arr, len(params), int(hbm_budget),
+                                                              ctypes.c_void_p(stream), ctypes.byref(b)))
+    return b
+
+
+def cascade_batch_admit(b, params: dict, nsteps: int) -> int:
+    slot = ctypes.c_int32()
+    cp = make_params(params)
+    check("cascade_batch_admit", load().cascade_batch_admit(b, ctypes.byref(cp), int(nsteps), ctypes.byref(slot)))
+    return slot.value
+
+
+def cascade_batch_step(b, nsteps_each) -> None:
+    a = np.ascontiguousarray(nsteps_each, dtype=np.int32)
+    check("cascade_batch_step", load().cascade_batch_step(b, a.ctypes.data))
+
+
+def cascade_batch_run(b, nsteps: int) -> None:
+    check("cascade_batch_run", load().cascade_batch_run(b, int(nsteps)))
+
+
+def cascade_batch_poll(b, max_n: int, wait: bool = False) -> list:
+    buf = np.zeros(max(max_n, 1), np.int32)
+    n = ctypes.c_int32()
+    check("cascade_batch_poll", load().cascade_batch_poll(b, buf.ctypes.data, int(max_n), ctypes.byref(n),
+                                                          1 if wait else 0))
+    return [int(x) for x in buf[: n.value]]
+
+
+def cascade_batch_diag(b, slot: int, max_records: int, nx: int | None = None, fields: bool = False):
+    buf = (cascade_diag_t * max(max_records, 1))()
+    n = ctypes.c_int32()
+    E = J = None
+    if fields:
+        E = np.zeros(nx)
+        J = np.zeros(nx)
+    check("cascade_batch_diag", load().cascade_batch_diag(b, int(slot), buf, int(max_records), ctypes.byref(n),
+                                                          _ptr(E), _ptr(J)))
+    a = np.frombuffer(buf, dtype=DIAG_DTYPE)[: n.value]
+    rec = {f: a[f].copy() for f in DIAG_FIELDS}
+    return (rec, E, J) if fields else rec
+
+
+def cascade_batch_counts(b, slot: int) -> dict:
+    v = [ctypes.c_int64() for _ in range(4)]
+    check("cascade_batch_counts", load().cascade_batch_counts(b, int(slot), *[ctypes.byref(x) for x in v]))
+    return dict(zip(("n_elec", "n_posi", "n_photon", "step"), (x.value for x in v)))
+
+
+def cascade_batch_release(b, slot: int) -> None:
+    check("cascade_batch_release", load().cascade_batch_release(b, int(slot)))
+
+
+def cascade_batch_info(b) -> dict:
+    s, o, u = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+    check("cascade_batch_info", load().cascade_batch_info(b, ctypes.byref(s), ctypes.byref(o), ctypes.byref(u)))
+    return {"slots": s.value, "occupied": o.value, "bytes": u.value}
+
+
+def cascade_batch_destroy(b) -> None:
+    if b:
+        check("cascade_batch_destroy", load().cascade_batch_destroy(b))

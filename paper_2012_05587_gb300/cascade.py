@@ -78,3 +78,72 @@ class Cascade:
 
 def diag_to_arrays(rec: dict) -> dict:
     return {k: np.asarray(v) for k, v in rec.items()}
+
+
+class CascadeBatch:
+    """Many cascades advanced together (one launch per kernel per step).
+
+    Either ``CascadeBatch(params_list)`` (every member in its initial state,
+    advanced with ``step``), or ``CascadeBatch(slots=..., precision=...,
+    max_nx=...)`` for admission-driven serving (``admit``/``run``/``poll``).
+    """
+
+    def __init__(self, params: list | None = None, *, slots: int = 0, precision="fp32", max_nx: int = 0,
+                 hbm_budget: int = 0, stream: int | None = None, torch_memory: bool = True):
+        if torch_memory:
+            capi.use_torch_allocator()
+        self.stream = _torch_stream() if stream is None else int(stream)
+        self.params = {}
+        if params is not None:
+            self.b = capi.cascade_batch_create(params, hbm_budget, self.stream)
+            self.params = {i: dict(p) for i, p in enumerate(params)}
+        else:
+            self.b = capi.cascade_batch_create_slots(slots, precision, max_nx, hbm_budget, self.stream)
+
+    def admit(self, params: dict, nsteps: int) -> int:
+        slot = capi.cascade_batch_admit(self.b, params, nsteps)
+        self.params[slot] = dict(params)
+        return slot
+
+    def step(self, nsteps_each) -> None:
+        capi.cascade_batch_step(self.b, nsteps_each)
+
+    def run(self, nsteps: int) -> None:
+        capi.cascade_batch_run(self.b, nsteps)
+
+    def poll(self, wait: bool = False, max_n: int = 4096) -> list:
+        return capi.cascade_batch_poll(self.b, max_n, wait)
+
+    def diag(self, slot: int, max_records: int = 1 << 16) -> dict:
+        return capi.cascade_batch_diag(self.b, slot, max_records)
+
+    def fields(self, slot: int):
+        _, E, J = capi.cascade_batch_diag(self.b, slot, 0, int(self.params[slot]["nx"]), fields=True)
+        return E, J
+
+    def counts(self, slot: int) -> dict:
+        return capi.cascade_batch_counts(self.b, slot)
+
+    def release(self, slot: int) -> None:
+        capi.cascade_batch_release(self.b, slot)
+        self.params.pop(slot, None)
+
+    def info(self) -> dict:
+        return capi.cascade_batch_info(self.b)
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            capi.cascade_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -150,7 +150,7 @@ Plan plan_of(const cascade_params* p) {
   return pl;
 }
 
-int setup(const cascade_params* params, void* stream, cascade_t** out) {
+int setup(const cascade_params* params, void* stream, cascade_t** out, bool batch_member = false) {
   *out = nullptr;
   int rc = validate(params);
   if (rc) return rc;
@@ -207,12 +207,19 @@ int setup(const cascade_params* params, void* stream, cascade_t** out) {
   d.E = static_cast<double*>(h->dalloc(sizeof(double) * d.nx));
   d.J = static_cast<double*>(h->dalloc(sizeof(double) * d.nx));
   const size_t acc = params->precision == CASCADE_FP64 ? partial_bytes_fp64() : partial_bytes_fp32();
-  if (d.variant == kSmemESmemS) {
+  if (d.variant == kSmemESmemS && !batch_member) {
     d.S_part = h->dalloc(acc * (size_t)d.grid_push * d.nxp);
     if (!d.S_part) return CASCADE_ERR_OOM;
   } else {
+    // global FP64 current: the single-cascade fallback variants and every
+    // batch member (its work items add their currents here)
     d.S_glob = static_cast<double*>(h->dalloc(sizeof(double) * d.nx));
     if (!d.S_glob) return CASCADE_ERR_OOM;
+  }
+  {
+    long long it = 4LL * d.nx;
+    if (it < 8192) it = 8192;
+    d.item_size = (it + 3) & ~3LL;
   }
   d.uk_part = static_cast<double*>(h->dalloc(sizeof(double) * d.grid_push));
   d.diag_part = static_cast<double*>(h->dalloc(sizeof(double) * 4 * d.grid_field));
@@ -229,6 +236,7 @@ int setup(const cascade_params* params, void* stream, cascade_t** out) {
   CUDA_TRY(cudaMemsetAsync(d.emit_end, 0, sizeof(long long) * (d.n_pp + 1), h->stream));
   CUDA_TRY(cudaMemsetAsync(d.ring, 0, sizeof(cascade_diag_t) * d.ring_n, h->stream));
   CUDA_TRY(cudaMemsetAsync(d.J, 0, sizeof(double) * d.nx, h->stream));
+  CUDA_TRY(cudaMemsetAsync(d.uk_part, 0, sizeof(double) * d.grid_push, h->stream));
   if (d.S_glob) CUDA_TRY(cudaMemsetAsync(d.S_glob, 0, sizeof(double) * d.nx, h->stream));
   return CASCADE_OK;
 }
@@ -305,23 +313,11 @@ int capture_graph(cascade_t* h) {
   return CASCADE_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int cascade_set_allocator(cascade_alloc_fn alloc_fn, cascade_free_fn free_fn, void* ctx) {
-  if ((alloc_fn == nullptr) != (free_fn == nullptr)) return CASCADE_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lk(g_alloc_mu);
-  g_alloc = alloc_fn;
-  g_free = free_fn;
-  g_ctx = ctx;
-  return CASCADE_OK;
-}
-
-int cascade_create(const cascade_params* params, void* cuda_stream, cascade_t** out) {
-  if (!out) return CASCADE_ERR_INVALID_ARG;
+// Section 3 initial state (uniform E0, quiet-start pairs, seeded momenta).
+int create_seeded(const cascade_params* params, void* cuda_stream, bool batch_member, cascade_t** out) {
+  *out = nullptr;
   cascade_t* h = nullptr;
-  int rc = setup(params, cuda_stream, &h);
+  int rc = setup(params, cuda_stream, &h, batch_member);
   if (rc == CASCADE_OK) {
     const long long npairs = (long long)params->nx * params->ppc;
     if (npairs > params->particle_cap) {
@@ -344,6 +340,24 @@ int cascade_create(const cascade_params* params, void* cuda_stream, cascade_t** 
   }
   *out = h;
   return CASCADE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cascade_set_allocator(cascade_alloc_fn alloc_fn, cascade_free_fn free_fn, void* ctx) {
+  if ((alloc_fn == nullptr) != (free_fn == nullptr)) return CASCADE_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc_fn;
+  g_free = free_fn;
+  g_ctx = ctx;
+  return CASCADE_OK;
+}
+
+int cascade_create(const cascade_params* params, void* cuda_stream, cascade_t** out) {
+  if (!out) return CASCADE_ERR_INVALID_ARG;
+  return create_seeded(params, cuda_stream, false, out);
 }
 
 int cascade_create_from_state(const cascade_params* params, int64_t n_elec, const int32_t* cell_e,
@@ -558,5 +572,392 @@ void set_error_message(const char* msg) { snprintf(g_msg, sizeof(g_msg), "%s", m
 }  // namespace cpic
 
 extern "C" {
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of cascades.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kSnapRing = 4;  // remaining-count snapshots in flight
+
+}  // namespace
+
+struct cascade_batch {
+  int n_slots = 0;
+  int precision = CASCADE_FP32_MIXED;
+  int max_nx = 0;
+  size_t budget = 0;
+  size_t used = 0;
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;       // caller's stream: all batch steps
+  cudaStream_t init_stream = nullptr;  // private: member allocation and seeding
+  cudaStream_t cap_stream = nullptr;   // private: graph capture
+  cudaGraphExec_t graph = nullptr;
+  std::vector<cascade_t*> members;
+  std::vector<long long> admit_seq;    // run sequence number at admission
+  std::vector<char> reported;
+  // device tables
+  Dev* d_devs = nullptr;
+  long long* d_remaining = nullptr;
+  long long* d_item_start = nullptr;
+  unsigned long long* d_work = nullptr;
+  void* d_block = nullptr;             // one allocation holding the tables
+  // pinned host mirrors
+  Dev* h_devs = nullptr;
+  long long* h_set = nullptr;          // staging for remaining-count updates
+  long long* h_snap[kSnapRing] = {nullptr};
+  cudaEvent_t ev_snap[kSnapRing] = {nullptr};
+  long long snap_seq[kSnapRing] = {0};
+  long long run_seq = 0;               // runs enqueued so far
+  int snap_next = 0;
+  cudaEvent_t ev_init = nullptr;
+  BatchDev bd{};
+  int grid = 0, block = 0, dep = 0;
+  size_t smem = 0;
+
+  cudaError_t launch_step() const {
+    return precision == CASCADE_FP64 ? batch_step_fp64(bd, grid, block, smem, dep, stream)
+                                     : batch_step_fp32(bd, grid, block, smem, dep, stream);
+  }
+};
+
+namespace {
+
+int batch_capture(cascade_batch_t* b) {
+  if (!b->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k)
+    e = b->precision == CASCADE_FP64 ? batch_step_fp64(b->bd, b->grid, b->block, b->smem, b->dep, b->cap_stream)
+                                     : batch_step_fp32(b->bd, b->grid, b->block, b->smem, b->dep, b->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(e, "capture batch step");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return CASCADE_OK;
+}
+
+// Queue nsteps batch steps and a snapshot of the remaining counts.
+int batch_enqueue(cascade_batch_t* b, int nsteps) {
+  int left = nsteps;
+  if (left >= kGraphSteps && !b->graph) {
+    int rc = batch_capture(b);
+    if (rc) return rc;
+  }
+  while (left >= kGraphSteps) {
+    CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+    left -= kGraphSteps;
+  }
+  for (; left > 0; --left) CUDA_TRY(b->launch_step());
+  const int k = b->snap_next;
+  // the slot's previous snapshot must have landed before it is overwritten
+  CUDA_TRY(cudaEventSynchronize(b->ev_snap[k]));
+  b->run_seq += 1;
+  CUDA_TRY(cudaMemcpyAsync(b->h_snap[k], b->d_remaining, sizeof(long long) * b->n_slots, cudaMemcpyDeviceToHost,
+                           b->stream));
+  CUDA_TRY(cudaEventRecord(b->ev_snap[k], b->stream));
+  b->snap_seq[k] = b->run_seq;
+  b->snap_next = (k + 1) % kSnapRing;
+  return CASCADE_OK;
+}
+
+int batch_member_check(cascade_batch_t* b, int slot) {
+  if (!b || slot < 0 || slot >= b->n_slots || !b->members[slot]) return CASCADE_ERR_INVALID_ARG;
+  return CASCADE_OK;
+}
+
+bool same_kernel_class(int a, int c) { return (a == CASCADE_FP64) == (c == CASCADE_FP64) && a == c; }
+
+}  // namespace
+
+extern "C" {
+
+int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max_nx, size_t hbm_budget,
+                               void* cuda_stream, cascade_batch_t** out) {
+  if (!out || max_slots < 1 || max_nx < 2 ||
+      (precision != CASCADE_FP64 && precision != CASCADE_FP32_MIXED && precision != CASCADE_FP32_MIXED_FINE))
+    return CASCADE_ERR_INVALID_ARG;
+  *out = nullptr;
+  cascade_batch_t* b = new (std::nothrow) cascade_batch_t();
+  if (!b) return CASCADE_ERR_OOM;
+  b->n_slots = max_slots;
+  b->precision = precision;
+  b->max_nx = max_nx;
+  b->budget = hbm_budget;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->members.assign(max_slots, nullptr);
+  b->admit_seq.assign(max_slots, 0);
+  b->reported.assign(max_slots, 0);
+  auto fail = [&](int code) {
+    cascade_batch_destroy(b);
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGetDevice"));
+  e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
+  const int fine = precision == CASCADE_FP32_MIXED_FINE ? 1 : 0;
+  e = precision == CASCADE_FP64
+          ? batch_configure_fp64(max_nx, 0, b->num_sms, &b->grid, &b->block, &b->smem, &b->dep)
+          : batch_configure_fp32(max_nx, fine, b->num_sms, &b->grid, &b->block, &b->smem, &b->dep);
+  if (e == cudaErrorInvalidValue) {
+    snprintf(g_msg, sizeof(g_msg), "max_nx = %d does not fit the batch kernel's shared memory", max_nx);
+    return fail(CASCADE_ERR_INVALID_ARG);
+  }
+  if (e != cudaSuccess) return fail(cuda_fail(e, "batch configure"));
+  // device tables in one allocation
+  const size_t n = (size_t)max_slots;
+  const size_t b_devs = (sizeof(Dev) * n + 255) & ~size_t(255);
+  const size_t b_rem = (sizeof(long long) * n + 255) & ~size_t(255);
+  const size_t b_items = (sizeof(long long) * (n + 1) + 255) & ~size_t(255);
+  const size_t total = b_devs + b_rem + b_items + 256;
+  e = cudaMalloc(&b->d_block, total);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc batch tables"));
+  char* base = static_cast<char*>(b->d_block);
+  b->d_devs = reinterpret_cast<Dev*>(base);
+  b->d_remaining = reinterpret_cast<long long*>(base + b_devs);
+  b->d_item_start = reinterpret_cast<long long*>(base + b_devs + b_rem);
+  b->d_work = reinterpret_cast<unsigned long long*>(base + b_devs + b_rem + b_items);
+  if ((e = cudaMemsetAsync(b->d_block, 0, total, b->stream)) != cudaSuccess) return fail(cuda_fail(e, "memset"));
+  if ((e = cudaMallocHost(&b->h_devs, sizeof(Dev) * n)) != cudaSuccess) return fail(cuda_fail(e, "host mirror"));
+  memset(b->h_devs, 0, sizeof(Dev) * n);
+  if ((e = cudaMallocHost(&b->h_set, sizeof(long long) * n)) != cudaSuccess) return fail(cuda_fail(e, "staging"));
+  for (int k = 0; k < kSnapRing; ++k) {
+    if ((e = cudaMallocHost(&b->h_snap[k], sizeof(long long) * n)) != cudaSuccess) return fail(cuda_fail(e, "snap"));
+    memset(b->h_snap[k], 0, sizeof(long long) * n);
+    if ((e = cudaEventCreateWithFlags(&b->ev_snap[k], cudaEventDisableTiming)) != cudaSuccess)
+      return fail(cuda_fail(e, "event"));
+  }
+  if ((e = cudaEventCreateWithFlags(&b->ev_init, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(cuda_fail(e, "event"));
+  if ((e = cudaStreamCreateWithFlags(&b->init_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail(cuda_fail(e, "stream"));
+  b->bd.devs = b->d_devs;
+  b->bd.remaining = b->d_remaining;
+  b->bd.item_start = b->d_item_start;
+  b->bd.work_next = b->d_work;
+  b->bd.n = max_slots;
+  b->bd.max_nx = max_nx;
+  if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return fail(cuda_fail(e, "sync"));
+  *out = b;
+  return CASCADE_OK;
+}
+
+int cascade_batch_admit(cascade_batch_t* b, const cascade_params* params, int32_t nsteps, int32_t* slot_out) {
+  if (!b || !params || nsteps < 0) return CASCADE_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  int rc = validate(params);
+  if (rc) return rc;
+  if (!same_kernel_class(params->precision, b->precision)) {
+    snprintf(g_msg, sizeof(g_msg), "member precision %d differs from the batch's %d", params->precision,
+             b->precision);
+    return CASCADE_ERR_INVALID_ARG;
+  }
+  if (params->nx > b->max_nx) {
+    snprintf(g_msg, sizeof(g_msg), "member nx = %d exceeds the batch's max_nx = %d", params->nx, b->max_nx);
+    return CASCADE_ERR_INVALID_ARG;
+  }
+  size_t need = 0;
+  cascade_footprint(params, nullptr, &need);
+  if (b->budget && b->used + need > b->budget) {
+    snprintf(g_msg, sizeof(g_msg), "footprint %zu B over the remaining budget %zu B", need, b->budget - b->used);
+    return CASCADE_ERR_BUSY;
+  }
+  int slot = -1;
+  for (int i = 0; i < b->n_slots; ++i)
+    if (!b->members[i]) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) {
+    snprintf(g_msg, sizeof(g_msg), "all %d slots are occupied", b->n_slots);
+    return CASCADE_ERR_BUSY;
+  }
+  cascade_t* h = nullptr;
+  rc = create_seeded(params, (void*)b->init_stream, true, &h);
+  if (rc) return rc;
+  b->members[slot] = h;
+  b->used += h->bytes;
+  b->reported[slot] = 0;
+  b->admit_seq[slot] = b->run_seq;
+  // publish the member: its initialisation (on the private stream) happens
+  // before the table update and every later step on the batch stream
+  CUDA_TRY(cudaEventRecord(b->ev_init, b->init_stream));
+  CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev_init, 0));
+  b->h_devs[slot] = h->d;
+  b->h_set[slot] = nsteps;
+  CUDA_TRY(cudaMemcpyAsync(b->d_devs + slot, b->h_devs + slot, sizeof(Dev), cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(cudaMemcpyAsync(b->d_remaining + slot, b->h_set + slot, sizeof(long long), cudaMemcpyHostToDevice,
+                           b->stream));
+  if (slot_out) *slot_out = slot;
+  return CASCADE_OK;
+}
+
+int cascade_batch_create(const cascade_params* params, int32_t n, size_t hbm_budget, void* cuda_stream,
+                         cascade_batch_t** out) {
+  if (!params || n < 1 || !out) return CASCADE_ERR_INVALID_ARG;
+  int max_nx = 2;
+  for (int i = 0; i < n; ++i) {
+    if (!same_kernel_class(params[i].precision, params[0].precision)) return CASCADE_ERR_INVALID_ARG;
+    if (params[i].nx > max_nx) max_nx = params[i].nx;
+  }
+  cascade_batch_t* b = nullptr;
+  int rc = cascade_batch_create_slots(n, params[0].precision, max_nx, hbm_budget, cuda_stream, &b);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    int slot = -1;
+    rc = cascade_batch_admit(b, &params[i], 0, &slot);
+    if (rc) {
+      cascade_batch_destroy(b);
+      return rc;
+    }
+  }
+  *out = b;
+  return CASCADE_OK;
+}
+
+int cascade_batch_step(cascade_batch_t* b, const int32_t* nsteps_each) {
+  if (!b || !nsteps_each) return CASCADE_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  // current remaining counts, then add the new targets
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  CUDA_TRY(cudaMemcpy(b->h_set, b->d_remaining, sizeof(long long) * b->n_slots, cudaMemcpyDeviceToHost));
+  long long most = 0;
+  for (int i = 0; i < b->n_slots; ++i) {
+    if (!b->members[i]) continue;
+    if (nsteps_each[i] < 0) return CASCADE_ERR_INVALID_ARG;
+    b->h_set[i] += nsteps_each[i];
+    if (b->h_set[i] > most) most = b->h_set[i];
+    if (nsteps_each[i] > 0) {
+      b->reported[i] = 0;
+      b->admit_seq[i] = b->run_seq;
+    }
+  }
+  CUDA_TRY(cudaMemcpyAsync(b->d_remaining, b->h_set, sizeof(long long) * b->n_slots, cudaMemcpyHostToDevice,
+                           b->stream));
+  while (most > 0) {
+    const int k = most > (1 << 30) ? (1 << 30) : (int)most;
+    int rc = batch_enqueue(b, k);
+    if (rc) return rc;
+    most -= k;
+  }
+  return CASCADE_OK;
+}
+
+int cascade_batch_run(cascade_batch_t* b, int32_t nsteps) {
+  if (!b || nsteps < 0) return CASCADE_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  return batch_enqueue(b, nsteps);
+}
+
+int cascade_batch_poll(cascade_batch_t* b, int32_t* done_slots, int32_t max, int32_t* n_out, int32_t wait) {
+  if (!b || max < 0 || (max > 0 && !done_slots)) return CASCADE_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  int best = -1;
+  if (wait) {
+    // all queued work, then a fresh snapshot
+    const int rc = batch_enqueue(b, 0);
+    if (rc) return rc;
+    const int k = (b->snap_next + kSnapRing - 1) % kSnapRing;
+    CUDA_TRY(cudaEventSynchronize(b->ev_snap[k]));
+    best = k;
+  } else {
+    for (int k = 0; k < kSnapRing; ++k) {
+      if (b->snap_seq[k] == 0) continue;
+      const cudaError_t q = cudaEventQuery(b->ev_snap[k]);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return cuda_fail(q, "cudaEventQuery");
+      if (best < 0 || b->snap_seq[k] > b->snap_seq[best]) best = k;
+    }
+  }
+  int n = 0;
+  if (best >= 0) {
+    const long long seq = b->snap_seq[best];
+    for (int i = 0; i < b->n_slots && n < max; ++i) {
+      if (!b->members[i] || b->reported[i]) continue;
+      // only snapshots queued after the member's admission speak for it
+      if (seq <= b->admit_seq[i]) continue;
+      if (b->h_snap[best][i] == 0) {
+        done_slots[n++] = i;
+        b->reported[i] = 1;
+      }
+    }
+  }
+  if (n_out) *n_out = n;
+  return CASCADE_OK;
+}
+
+int cascade_batch_diag(cascade_batch_t* b, int32_t slot, cascade_diag_t* host_out, int32_t max, int32_t* n_out,
+                       double* E_host, double* J_host) {
+  int rc = batch_member_check(b, slot);
+  if (rc) return rc;
+  cudaSetDevice(b->device);
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return cascade_diag(b->members[slot], host_out, max, n_out, E_host, J_host);
+}
+
+int cascade_batch_counts(cascade_batch_t* b, int32_t slot, int64_t* n_elec, int64_t* n_posi, int64_t* n_photon,
+                         int64_t* step) {
+  int rc = batch_member_check(b, slot);
+  if (rc) return rc;
+  cudaSetDevice(b->device);
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return cascade_counts(b->members[slot], n_elec, n_posi, n_photon, step);
+}
+
+int cascade_batch_release(cascade_batch_t* b, int32_t slot) {
+  int rc = batch_member_check(b, slot);
+  if (rc) return rc;
+  cudaSetDevice(b->device);
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  b->h_set[slot] = 0;
+  CUDA_TRY(cudaMemcpy(b->d_remaining + slot, b->h_set + slot, sizeof(long long), cudaMemcpyHostToDevice));
+  cascade_t* h = b->members[slot];
+  b->used -= h->bytes;
+  b->members[slot] = nullptr;
+  b->reported[slot] = 0;
+  return cascade_destroy(h);
+}
+
+int cascade_batch_info(cascade_batch_t* b, int32_t* slots, int32_t* occupied, size_t* bytes_in_use) {
+  if (!b) return CASCADE_ERR_INVALID_ARG;
+  int occ = 0;
+  for (cascade_t* h : b->members) occ += h != nullptr;
+  if (slots) *slots = b->n_slots;
+  if (occupied) *occupied = occ;
+  if (bytes_in_use) *bytes_in_use = b->used;
+  return CASCADE_OK;
+}
+
+int cascade_batch_destroy(cascade_batch_t* b) {
+  if (!b) return CASCADE_OK;
+  cudaSetDevice(b->device);
+  if (b->stream || b->d_block) cudaStreamSynchronize(b->stream);
+  if (b->init_stream) cudaStreamSynchronize(b->init_stream);
+  for (cascade_t* h : b->members)
+    if (h) cascade_destroy(h);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->init_stream) cudaStreamDestroy(b->init_stream);
+  for (int k = 0; k < kSnapRing; ++k) {
+    if (b->ev_snap[k]) cudaEventDestroy(b->ev_snap[k]);
+    if (b->h_snap[k]) cudaFreeHost(b->h_snap[k]);
+  }
+  if (b->ev_init) cudaEventDestroy(b->ev_init);
+  if (b->h_devs) cudaFreeHost(b->h_devs);
+  if (b->h_set) cudaFreeHost(b->h_set);
+  if (b->d_block) cudaFree(b->d_block);
+  delete b;
+  return CASCADE_OK;
+}
 
 }  // extern "C"

@@ -64,6 +64,17 @@ struct Dev {
   int push_fast;       // 1: gamma from one reciprocal square root (FP32 only)
   int fine_deposit;    // FP32: two-word accumulator (CASCADE_FP32_MIXED_FINE)
   long long min_per_cta;  // particles per active CTA before another CTA is woken
+  long long item_size;    // batched kernels: particles per work item (multiple of 4)
+};
+
+// A batch of cascades advanced together (one launch per kernel per step).
+struct BatchDev {
+  const Dev* devs;               // [n] member descriptors
+  long long* remaining;          // [n] steps left per member; 0 = idle or empty slot
+  long long* item_start;         // [n + 1] first work item of each member in this step
+  unsigned long long* work_next; // next work item to hand out
+  int n;                         // slots
+  int max_nx;                    // largest member grid (shared-memory sizing)
 };
 
 enum PushVariant {
@@ -86,6 +97,10 @@ void set_error_message(const char* msg);
   cudaError_t step_timed_##SUFFIX(const Dev& d, cudaStream_t s, cudaEvent_t before, cudaEvent_t after); \
   cudaError_t gauss_##SUFFIX(const Dev& d, double* rho_dx, double* out, cudaStream_t s);       \
   cudaError_t configure_##SUFFIX(Dev& d, int num_sms);                                         \
+  cudaError_t batch_configure_##SUFFIX(int max_nx, int fine, int num_sms, int* grid, int* block,   \
+                                       size_t* smem, int* dep);                                 \
+  cudaError_t batch_step_##SUFFIX(const BatchDev& b, int grid, int block, size_t smem, int dep,   \
+                                  cudaStream_t s);                                              \
   size_t partial_bytes_##SUFFIX();
 
 CASCADE_DECLARE_LAUNCHERS(fp64)

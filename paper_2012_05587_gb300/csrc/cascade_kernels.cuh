@@ -211,10 +211,298 @@ struct AccOf<Real, 4> {
 };
 
 // ---------------------------------------------------------------------------
-// The particle kernel.  V: where E and the current accumulator live (see
-// PushVariant).  Four particles per thread and iteration: their eight E
-// loads are issued together, then the push/move of all four, then the
-// deposits, then (only if a lane crossed gamma_thr) the emissions.
+// The particle update, shared by the single-cascade and the batched kernels.
+// PushState holds what one CTA set up for one cascade: the shared-memory E and
+// current accumulator, the fixed-point scales, the photon-ring window.
+// ---------------------------------------------------------------------------
+template <class Real, int DEP>
+struct PushState {
+  typedef typename AccOf<Real, DEP>::type Acc;
+  Ctl* ctl;
+  Real* Es;
+  Acc* Ss;
+  int* Ls;
+  float fx_scale, fx_inv, lo_scale, lo_inv;
+  long long ph_tail, room, ph_mask;
+};
+
+// Fixed-point scales for a CTA that deposits at most pcount particles.  Every
+// contribution is below dt/dx in magnitude, so each edge's sum stays below
+// 2^30 at 2^k; the DEP 4 residual word sums pcount values of at most
+// 2^-(k+1) at a finer scale 2^(k+1+m), again below 2^30.
+template <class Real, int DEP>
+__device__ __forceinline__ void set_scales(PushState<Real, DEP>& st, double pcount, double dtdx) {
+  st.fx_scale = st.fx_inv = st.lo_scale = st.lo_inv = 1.0f;
+  if (DEP == 1 || DEP == 4) {
+    const double pc = pcount + 1.0;
+    int k = (int)floor(log2(1073741824.0 / (pc * dtdx + 1.0)));
+    k = k < 0 ? 0 : (k > 30 ? 30 : k);
+    st.fx_scale = ldexpf(1.0f, k);
+    st.fx_inv = ldexpf(1.0f, -k);
+    if (DEP == 4) {
+      int m = (int)floor(log2(1073741824.0 / pc));
+      m = m < 0 ? 0 : m;
+      int kl = k + 1 + m;
+      kl = kl > 60 ? 60 : kl;
+      st.lo_scale = ldexpf(1.0f, kl);
+      st.lo_inv = ldexpf(1.0f, -kl);
+    }
+  }
+}
+
+// Advance four consecutive particles of species s starting at index base
+// (cnt of them valid; the whole warp calls this together).  Returns the sum
+// of their gamma after the step.
+template <class Real, int V, int DEP, bool FAST>
+__device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP>& st, int s, long long base,
+                                         int cnt, int lane) {
+  typedef typename AccOf<Real, DEP>::type Acc;
+  const int nx = d.nx;
+  const Real dt = (Real)d.dt, dtdx = (Real)d.dtdx;
+  const Real thr = (Real)d.gamma_thr, eps = (Real)d.eps_gamma, lpf = (Real)d.lpp_frac;
+  const Real one = Real(1), half = Real(0.5), zero = Real(0);
+  int* cellp = d.cell[s] + base;
+  Real* offp = static_cast<Real*>(d.off[s]) + base;
+  Real* up = static_cast<Real*>(d.u[s]) + base;
+  int cl[4] = {0, 0, 0, 0};
+  Real of[4] = {zero, zero, zero, zero}, uu[4] = {zero, zero, zero, zero};
+  if (cnt == 4) {
+    ld4(cellp, cl);
+    ld4(offp, of);
+    ld4(up, uu);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j < cnt) {
+        cl[j] = cellp[j];
+        of[j] = offp[j];
+        uu[j] = up[j];
+      }
+    }
+  }
+  const Real q = s ? one : -one;
+  const Real qdt = s ? dt : -dt;
+
+  // gather: linear between the two edges bracketing each particle
+  Real Ep[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = cl[j];
+    const Real o = of[j];
+    const bool hi = o >= half;
+    const int ia = hi ? c : ((c == 0) ? nx - 1 : c - 1);
+    const int ib = hi ? ((c + 1 == nx) ? 0 : c + 1) : c;
+    const Real w = hi ? o - half : o + half;
+    Real Ea, Eb;
+    if (V == kGlobEGlobS) {
+      Ea = (Real)__ldg(d.E + ia);
+      Eb = (Real)__ldg(d.E + ib);
+    } else {
+      Ea = st.Es[ia];
+      Eb = st.Es[ib];
+    }
+    Ep[j] = (one - w) * Ea + w * Eb;
+  }
+
+  // push (du/dt = q E), move (dx/dt = u / gamma, cell units) and the
+  // charge-conserving current: q * (offset change) per edge crossed
+  Real g[4], a1[4], a2[4];
+  int e1[4], e2[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = cl[j];
+    const Real o = of[j];
+    const Real u = uu[j] + qdt * Ep[j];
+    Real gj, dd;
+    Kin<Real, FAST>::eval(u, dtdx, gj, dd);
+    Real o2 = o + dd;
+    int c2 = c;
+    Real b1, b2 = zero;
+    int f2 = -1;
+    if (o2 >= one) {
+      b1 = q * (one - o);
+      c2 = (c + 1 == nx) ? 0 : c + 1;
+      o2 = o2 - one;
+      f2 = c2;
+      b2 = q * o2;
+    } else if (o2 < zero) {
+      b1 = q * (zero - o);
+      c2 = (c == 0) ? nx - 1 : c - 1;
+      o2 = o2 + one;
+      f2 = c2;
+      b2 = q * (o2 - one);
+      if (o2 >= one) {
+        o2 = zero;
+        c2 = c;
+      }
+    } else {
+      b1 = q * (o2 - o);
+    }
+    const bool valid = j < cnt;
+    e1[j] = valid ? c : -1;
+    e2[j] = valid ? f2 : -1;
+    a1[j] = b1;
+    a2[j] = b2;
+    g[j] = valid ? gj : one;
+    cl[j] = c2;
+    of[j] = o2;
+    uu[j] = u;
+  }
+
+  // deposit
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (V == kSmemESmemS) {
+      if (DEP == 1) {
+        if (e1[j] >= 0) atomicAdd(&st.Ss[e1[j]], __float2int_rn((float)a1[j] * st.fx_scale));
+        if (e2[j] >= 0) atomicAdd(&st.Ss[e2[j]], __float2int_rn((float)a2[j] * st.fx_scale));
+      } else if (DEP == 4) {
+        if (e1[j] >= 0) {
+          const float a = (float)a1[j];
+          const int qh = __float2int_rn(a * st.fx_scale);
+          const int ql = __float2int_rn((a - (float)qh * st.fx_inv) * st.lo_scale);  // residual is exact
+          atomicAdd(&st.Ss[e1[j]], qh);
+          if (ql != 0) atomicAdd(&st.Ls[e1[j]], ql);
+        }
+        if (e2[j] >= 0) {
+          const float a = (float)a2[j];
+          const int qh = __float2int_rn(a * st.fx_scale);
+          const int ql = __float2int_rn((a - (float)qh * st.fx_inv) * st.lo_scale);
+          atomicAdd(&st.Ss[e2[j]], qh);
+          if (ql != 0) atomicAdd(&st.Ls[e2[j]], ql);
+        }
+      } else {
+        if (e1[j] >= 0) atomicAdd(&st.Ss[e1[j]], (Acc)a1[j]);
+        if (e2[j] >= 0) atomicAdd(&st.Ss[e2[j]], (Acc)a2[j]);
+      }
+    } else {
+      if (e1[j] >= 0) atomicAdd(&d.S_glob[e1[j]], (double)a1[j]);
+      if (e2[j] >= 0) atomicAdd(&d.S_glob[e2[j]], (double)a2[j]);
+    }
+  }
+
+  // QED (Section 2): threshold emission with recoil; photons appended with
+  // one warp-wide scan and one global atomic per slot that has emitters
+  const bool hot = (g[0] >= thr) | (g[1] >= thr) | (g[2] >= thr) | (g[3] >= thr) |
+                   !(g[0] <= Real(1e30)) | !(g[1] <= Real(1e30)) | !(g[2] <= Real(1e30)) |
+                   !(g[3] <= Real(1e30));
+  if (__any_sync(kFull, hot)) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int k = 0;
+      int enc = 0;
+      Real oc = zero;
+      Real u = uu[j], gj = g[j];
+      bool emit;
+      const bool fwd = u > zero;  // direction kept through the recoil
+      if (!(gj <= Real(1e30))) {
+        // non-finite or absurd gamma: the run has blown up; flag it, no emission
+        set_error(st.ctl, CASCADE_ERR_NONFINITE);
+        emit = false;
+      } else if (sizeof(Real) == 4 && gj > Real(1e6)) {
+        // large gamma: threshold test and recoil in FP64
+        const double ud = (double)u;
+        const double gd = sqrt(1.0 + ud * ud);
+        emit = gd >= d.gamma_thr;
+        if (emit) {
+          k = 1 + (int)fmin(floor((gd - d.gamma_thr) / d.eps_gamma), (double)kMaxPhotonsPerStep);
+          const double g2 = gd - (double)k * d.eps_gamma;
+          u = (Real)((fwd ? 1.0 : -1.0) * sqrt(g2 * g2 - 1.0));
+          gj = (Real)g2;
+        }
+      } else {
+        emit = gj >= thr;
+        if (emit) {
+          k = 1 + (int)fmin(floor((gj - thr) / eps), (Real)kMaxPhotonsPerStep);
+          const Real g2 = gj - (Real)k * eps;
+          const Real sg = fwd ? one : -one;
+          u = sg * sqrt(g2 * g2 - one);
+          gj = g2;
+        }
+      }
+      if (emit) {
+        // conversion point x + dir * l_pp, wrapped
+        const Real o2 = of[j];
+        const int c2 = cl[j];
+        long long ci;
+        if (fwd) {
+          oc = o2 + lpf;
+          ci = (long long)c2 + d.lpp_int;
+          if (oc >= one) {
+            oc = oc - one;
+            ci += 1;
+          }
+        } else {
+          oc = o2 - lpf;
+          ci = (long long)c2 - d.lpp_int;
+          if (oc < zero) {
+            oc = oc + one;
+            ci -= 1;
+            if (oc >= one) {
+              oc = zero;
+              ci += 1;
+            }
+          }
+        }
+        long long m = ci % nx;
+        if (m < 0) m += nx;
+        enc = (int)m | (fwd ? 0 : (int)0x80000000);
+        if (k > 1) atomicAdd(reinterpret_cast<unsigned long long*>(&st.ctl->emit_multi), 1ull);
+        uu[j] = u;
+        g[j] = gj;
+      }
+      const unsigned em = __ballot_sync(kFull, k > 0);
+      if (em) {
+        const unsigned long long kk = (unsigned long long)k;
+        unsigned long long incl = kk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long v = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const unsigned long long tot = __shfl_sync(kFull, incl, 31);
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&st.ctl->emit_count, tot);
+        b0 = __shfl_sync(kFull, b0, 0);
+        const unsigned long long first = b0 + incl - kk;
+        for (int m = 0; m < k; ++m) {
+          const unsigned long long pos = first + m;
+          if ((long long)pos < st.room) {
+            const long long slot = (st.ph_tail + (long long)pos) & st.ph_mask;
+            d.ph_cell[slot] = enc;
+            static_cast<Real*>(d.ph_off)[slot] = oc;
+          } else {
+            set_error(st.ctl, CASCADE_ERR_PHOTON_CAPACITY);
+          }
+        }
+      }
+    }
+  }
+
+  if (cnt == 4) {
+    st4(cellp, cl);
+    st4(offp, of);
+    st4(up, uu);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j < cnt) {
+        cellp[j] = cl[j];
+        offp[j] = of[j];
+        up[j] = uu[j];
+      }
+    }
+  }
+  Real gs = zero;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) gs += (j < cnt) ? g[j] : zero;
+  return gs;
+}
+
+// ---------------------------------------------------------------------------
+// The particle kernel of one cascade.  V: where E and the current accumulator
+// live (see PushVariant).  Persistent grid; the number of working CTAs
+// follows the particle count.
 // ---------------------------------------------------------------------------
 template <class Real, int V, int DEP, bool FAST>
 __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
@@ -227,16 +515,18 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
 
   const int nx = d.nx;
   const size_t eb = ((size_t)nx * sizeof(Real) + 15) & ~size_t(15);
-  Real* Es = reinterpret_cast<Real*>(smem_raw);
-  Acc* Ss = reinterpret_cast<Acc*>(smem_raw + eb);
-  int* Ls = reinterpret_cast<int*>(smem_raw + 2 * eb);  // DEP 4 fine word
+  PushState<Real, DEP> st;
+  st.ctl = ctl;
+  st.Es = reinterpret_cast<Real*>(smem_raw);
+  st.Ss = reinterpret_cast<Acc*>(smem_raw + eb);
+  st.Ls = reinterpret_cast<int*>(smem_raw + 2 * eb);  // DEP 4 residual word
   if (V != kGlobEGlobS) {
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) Es[i] = (Real)d.E[i];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) st.Es[i] = (Real)d.E[i];
   }
   if (V == kSmemESmemS) {
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      Ss[i] = Acc(0);
-      if (DEP == 4) Ls[i] = 0;
+      st.Ss[i] = Acc(0);
+      if (DEP == 4) st.Ls[i] = 0;
     }
   }
   __syncthreads();
@@ -244,47 +534,19 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
   const long long cc = ctl->conv_count;
   const long long N0 = ctl->n[0] + cc, N1 = ctl->n[1] + cc;
   const long long C0 = (N0 + 3) >> 2, C1 = (N1 + 3) >> 2, C = C0 + C1;
-  const long long ph_tail = ctl->ph_tail;
-  const long long room = d.ph_cap - (ph_tail - ctl->conv_end);
-  const long long ph_mask = d.ph_cap - 1;
+  st.ph_tail = ctl->ph_tail;
+  st.room = d.ph_cap - (st.ph_tail - ctl->conv_end);
+  st.ph_mask = d.ph_cap - 1;
   const long long stride = (long long)G * blockDim.x;
-
-  const Real dt = (Real)d.dt, dtdx = (Real)d.dtdx;
-  const Real thr = (Real)d.gamma_thr, eps = (Real)d.eps_gamma, lpf = (Real)d.lpp_frac;
-  const Real one = Real(1), half = Real(0.5), zero = Real(0);
-  Real* ph_off = static_cast<Real*>(d.ph_off);
-
-  // fixed-point scale: every contribution is below dtdx in magnitude and this
-  // CTA handles at most iters * blockDim * 4 particles, so the sum of any
-  // edge stays below 2^30
-  float fx_scale = 1.0f, fx_inv = 1.0f, lo_scale = 1.0f, lo_inv = 1.0f;
-  if (DEP == 1 || DEP == 4) {
-    const long long iters = (C + stride - 1) / stride;
-    const double pcta = (double)(iters * blockDim.x * 4) + 1.0;
-    int k = (int)floor(log2(1073741824.0 / (pcta * d.dtdx + 1.0)));
-    k = k < 0 ? 0 : (k > 30 ? 30 : k);
-    fx_scale = ldexpf(1.0f, k);
-    fx_inv = ldexpf(1.0f, -k);
-    if (DEP == 4) {
-      // residuals are at most 2^-(k+1): pcta of them stay below 2^30 at 2^(k+1+m)
-      int m = (int)floor(log2(1073741824.0 / pcta));
-      m = m < 0 ? 0 : m;
-      int kl = k + 1 + m;
-      kl = kl > 60 ? 60 : kl;
-      lo_scale = ldexpf(1.0f, kl);
-      lo_inv = ldexpf(1.0f, -kl);
-    }
-  }
+  const long long first_wb = (long long)blockIdx.x * blockDim.x;
+  const long long iters_cta = (C > first_wb) ? (C - first_wb + stride - 1) / stride : 0;
+  set_scales<Real, DEP>(st, (double)(iters_cta * blockDim.x * 4), d.dtdx);
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   double gsum_total = 0.0;
-
-  const long long first_wb = (long long)blockIdx.x * blockDim.x;
-  const long long iters_cta = (C > first_wb) ? (C - first_wb + stride - 1) / stride : 0;
   for (long long it = 0; it < iters_cta; ++it) {
-    const long long wb = first_wb + it * stride + warp * 32;
-    const long long ch = wb + lane;
+    const long long ch = first_wb + it * stride + warp * 32 + lane;
     int s = 0, cnt = 0;
     long long base = 0;
     if (ch < C) {
@@ -293,242 +555,7 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
       const long long N = s ? N1 : N0;
       cnt = (int)min(4LL, N - base);
     }
-    int* cellp = d.cell[s] + base;
-    Real* offp = static_cast<Real*>(d.off[s]) + base;
-    Real* up = static_cast<Real*>(d.u[s]) + base;
-    int cl[4] = {0, 0, 0, 0};
-    Real of[4] = {zero, zero, zero, zero}, uu[4] = {zero, zero, zero, zero};
-    if (cnt == 4) {
-      ld4(cellp, cl);
-      ld4(offp, of);
-      ld4(up, uu);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (j < cnt) {
-          cl[j] = cellp[j];
-          of[j] = offp[j];
-          uu[j] = up[j];
-        }
-      }
-    }
-    const Real q = s ? one : -one;
-    const Real qdt = s ? dt : -dt;
-
-    // gather: linear between the two edges bracketing each particle
-    Real Ep[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = cl[j];
-      const Real o = of[j];
-      const bool hi = o >= half;
-      const int ia = hi ? c : ((c == 0) ? nx - 1 : c - 1);
-      const int ib = hi ? ((c + 1 == nx) ? 0 : c + 1) : c;
-      const Real w = hi ? o - half : o + half;
-      Real Ea, Eb;
-      if (V == kGlobEGlobS) {
-        Ea = (Real)__ldg(d.E + ia);
-        Eb = (Real)__ldg(d.E + ib);
-      } else {
-        Ea = Es[ia];
-        Eb = Es[ib];
-      }
-      Ep[j] = (one - w) * Ea + w * Eb;
-    }
-
-    // push (du/dt = q E), move (dx/dt = u / gamma, cell units) and the
-    // charge-conserving current: q * (offset change) per edge crossed
-    Real g[4], a1[4], a2[4];
-    int e1[4], e2[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = cl[j];
-      const Real o = of[j];
-      const Real u = uu[j] + qdt * Ep[j];
-      Real gj, dd;
-      Kin<Real, FAST>::eval(u, dtdx, gj, dd);
-      Real o2 = o + dd;
-      int c2 = c;
-      Real b1, b2 = zero;
-      int f2 = -1;
-      if (o2 >= one) {
-        b1 = q * (one - o);
-        c2 = (c + 1 == nx) ? 0 : c + 1;
-        o2 = o2 - one;
-        f2 = c2;
-        b2 = q * o2;
-      } else if (o2 < zero) {
-        b1 = q * (zero - o);
-        c2 = (c == 0) ? nx - 1 : c - 1;
-        o2 = o2 + one;
-        f2 = c2;
-        b2 = q * (o2 - one);
-        if (o2 >= one) {
-          o2 = zero;
-          c2 = c;
-        }
-      } else {
-        b1 = q * (o2 - o);
-      }
-      const bool valid = j < cnt;
-      e1[j] = valid ? c : -1;
-      e2[j] = valid ? f2 : -1;
-      a1[j] = b1;
-      a2[j] = b2;
-      g[j] = valid ? gj : one;
-      cl[j] = c2;
-      of[j] = o2;
-      uu[j] = u;
-    }
-
-    // deposit
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (V == kSmemESmemS) {
-        if (DEP == 1) {
-          if (e1[j] >= 0) atomicAdd(&Ss[e1[j]], __float2int_rn((float)a1[j] * fx_scale));
-          if (e2[j] >= 0) atomicAdd(&Ss[e2[j]], __float2int_rn((float)a2[j] * fx_scale));
-        } else if (DEP == 4) {
-          if (e1[j] >= 0) {
-            const float a = (float)a1[j];
-            const int qh = __float2int_rn(a * fx_scale);
-            const int ql = __float2int_rn((a - (float)qh * fx_inv) * lo_scale);  // residual is exact
-            atomicAdd(&Ss[e1[j]], qh);
-            if (ql != 0) atomicAdd(&Ls[e1[j]], ql);
-          }
-          if (e2[j] >= 0) {
-            const float a = (float)a2[j];
-            const int qh = __float2int_rn(a * fx_scale);
-            const int ql = __float2int_rn((a - (float)qh * fx_inv) * lo_scale);
-            atomicAdd(&Ss[e2[j]], qh);
-            if (ql != 0) atomicAdd(&Ls[e2[j]], ql);
-          }
-        } else {
-          if (e1[j] >= 0) atomicAdd(&Ss[e1[j]], (Acc)a1[j]);
-          if (e2[j] >= 0) atomicAdd(&Ss[e2[j]], (Acc)a2[j]);
-        }
-      } else {
-        if (e1[j] >= 0) atomicAdd(&d.S_glob[e1[j]], (double)a1[j]);
-        if (e2[j] >= 0) atomicAdd(&d.S_glob[e2[j]], (double)a2[j]);
-      }
-    }
-
-    // QED (Section 2): threshold emission with recoil; photons appended with
-    // one warp-wide scan and one global atomic per slot that has emitters
-    const bool hot = (g[0] >= thr) | (g[1] >= thr) | (g[2] >= thr) | (g[3] >= thr) |
-                     !(g[0] <= Real(1e30)) | !(g[1] <= Real(1e30)) | !(g[2] <= Real(1e30)) |
-                     !(g[3] <= Real(1e30));
-    if (__any_sync(kFull, hot)) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        int k = 0;
-        int enc = 0;
-        Real oc = zero;
-        Real u = uu[j], gj = g[j];
-        bool emit;
-        const bool fwd = u > zero;  // direction kept through the recoil
-        if (!(gj <= Real(1e30))) {
-          // non-finite or absurd gamma: the run has blown up; flag it, no emission
-          set_error(ctl, CASCADE_ERR_NONFINITE);
-          emit = false;
-        } else if (sizeof(Real) == 4 && gj > Real(1e6)) {
-          // large gamma: threshold test and recoil in FP64
-          const double ud = (double)u;
-          const double gd = sqrt(1.0 + ud * ud);
-          emit = gd >= d.gamma_thr;
-          if (emit) {
-            k = 1 + (int)fmin(floor((gd - d.gamma_thr) / d.eps_gamma), (double)kMaxPhotonsPerStep);
-            const double g2 = gd - (double)k * d.eps_gamma;
-            u = (Real)((fwd ? 1.0 : -1.0) * sqrt(g2 * g2 - 1.0));
-            gj = (Real)g2;
-          }
-        } else {
-          emit = gj >= thr;
-          if (emit) {
-            k = 1 + (int)fmin(floor((gj - thr) / eps), (Real)kMaxPhotonsPerStep);
-            const Real g2 = gj - (Real)k * eps;
-            const Real sg = fwd ? one : -one;
-            u = sg * sqrt(g2 * g2 - one);
-            gj = g2;
-          }
-        }
-        if (emit) {
-          // conversion point x + dir * l_pp, wrapped
-          const Real o2 = of[j];
-          const int c2 = cl[j];
-          long long ci;
-          if (fwd) {
-            oc = o2 + lpf;
-            ci = (long long)c2 + d.lpp_int;
-            if (oc >= one) {
-              oc = oc - one;
-              ci += 1;
-            }
-          } else {
-            oc = o2 - lpf;
-            ci = (long long)c2 - d.lpp_int;
-            if (oc < zero) {
-              oc = oc + one;
-              ci -= 1;
-              if (oc >= one) {
-                oc = zero;
-                ci += 1;
-              }
-            }
-          }
-          long long m = ci % nx;
-          if (m < 0) m += nx;
-          enc = (int)m | (fwd ? 0 : (int)0x80000000);
-          if (k > 1) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->emit_multi), 1ull);
-          uu[j] = u;
-          g[j] = gj;
-        }
-        const unsigned em = __ballot_sync(kFull, k > 0);
-        if (em) {
-          const unsigned long long kk = (unsigned long long)k;
-          unsigned long long incl = kk;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
-          }
-          const unsigned long long tot = __shfl_sync(kFull, incl, 31);
-          unsigned long long b0 = 0;
-          if (lane == 0) b0 = atomicAdd(&ctl->emit_count, tot);
-          b0 = __shfl_sync(kFull, b0, 0);
-          const unsigned long long first = b0 + incl - kk;
-          for (int m = 0; m < k; ++m) {
-            const unsigned long long pos = first + m;
-            if ((long long)pos < room) {
-              const long long slot = (ph_tail + (long long)pos) & ph_mask;
-              d.ph_cell[slot] = enc;
-              ph_off[slot] = oc;
-            } else {
-              set_error(ctl, CASCADE_ERR_PHOTON_CAPACITY);
-            }
-          }
-        }
-      }
-    }
-
-    if (cnt == 4) {
-      st4(cellp, cl);
-      st4(offp, of);
-      st4(up, uu);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (j < cnt) {
-          cellp[j] = cl[j];
-          offp[j] = of[j];
-          up[j] = uu[j];
-        }
-      }
-    }
-    Real gs = zero;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) gs += (j < cnt) ? g[j] : zero;
-    gsum_total += (double)gs;
+    gsum_total += (double)process4<Real, V, DEP, FAST>(d, st, s, base, cnt, lane);
   }
 
   // sum of gamma over the CTA (FP64)
@@ -545,9 +572,9 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
   if (V == kSmemESmemS) {
     Real* P = static_cast<Real*>(d.S_part) + (size_t)blockIdx.x * d.nxp;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      if (DEP == 1) P[i] = (Real)((float)Ss[i] * fx_inv);
-      else if (DEP == 4) P[i] = (Real)((double)Ss[i] * (double)fx_inv + (double)Ls[i] * (double)lo_inv);
-      else P[i] = (Real)Ss[i];
+      if (DEP == 1) P[i] = (Real)((float)st.Ss[i] * st.fx_inv);
+      else if (DEP == 4) P[i] = (Real)((double)st.Ss[i] * (double)st.fx_inv + (double)st.Ls[i] * (double)st.lo_inv);
+      else P[i] = (Real)st.Ss[i];
     }
   }
 }
@@ -586,6 +613,46 @@ __device__ __forceinline__ void block_reduce4(double v[4], double* sh /* [4][32]
     }
   }
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// End of a step (one thread): pairs and photons of this step join the
+// counters, the step advances, the per-step record is written.  r holds
+// sum E, sum J, max |E|, U_E over the edges; gsum is the sum of gamma.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void finish_step(const Dev& d, const double r[4], double gsum) {
+  Ctl* ctl = d.ctl;
+  const long long cc = ctl->conv_count;
+  ctl->n[0] += cc;
+  ctl->n[1] += cc;
+  ctl->pairs_total += cc;
+  ctl->ph_head = ctl->conv_end;
+  unsigned long long em = ctl->emit_count;
+  const long long room = d.ph_cap - (ctl->ph_tail - ctl->conv_end);
+  if ((long long)em > room) em = (unsigned long long)room;
+  ctl->ph_tail += (long long)em;
+  d.emit_end[ctl->step % (d.n_pp + 1)] = ctl->ph_tail;
+  ctl->emit_count = 0ull;
+  ctl->conv_count = 0;
+  ctl->step += 1;
+  const long long st = ctl->step;
+  cascade_diag_t rec;
+  rec.step = st;
+  rec.t = (double)st * d.dt;
+  rec.E_mean = r[0] / d.nx;
+  rec.J_mean = r[1] / d.nx;
+  rec.E_absmax = r[2];
+  rec.U_E = r[3];
+  rec.U_K = d.w * gsum;
+  const long long nph = ctl->ph_tail - ctl->ph_head;
+  rec.U_gamma = (double)nph * d.w * d.eps_gamma;
+  rec.gauss_resid = __longlong_as_double(0x7ff8000000000000LL);
+  rec.n_elec = ctl->n[0];
+  rec.n_posi = ctl->n[1];
+  rec.n_photon = nph;
+  rec.n_pairs_total = ctl->pairs_total;
+  rec.n_emit_multi = ctl->emit_multi;
+  d.ring[(st - 1) % d.ring_n] = rec;
 }
 
 template <class Acc, bool kPartials>
@@ -653,38 +720,240 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(Dev d) {
   for (int b = threadIdx.x; b < G; b += blockDim.x) gs[0] += __ldcg(d.uk_part + b);
   block_reduce4(gs, sh);
   if (threadIdx.x == 0) {
-    const long long cc = ctl->conv_count;
-    ctl->n[0] += cc;
-    ctl->n[1] += cc;
-    ctl->pairs_total += cc;
-    ctl->ph_head = ctl->conv_end;
-    unsigned long long em = ctl->emit_count;
-    const long long room = d.ph_cap - (ctl->ph_tail - ctl->conv_end);
-    if ((long long)em > room) em = (unsigned long long)room;
-    ctl->ph_tail += (long long)em;
-    d.emit_end[ctl->step % (d.n_pp + 1)] = ctl->ph_tail;
-    ctl->emit_count = 0ull;
-    ctl->conv_count = 0;
-    ctl->step += 1;
     ctl->field_ticket = 0u;
-    const long long st = ctl->step;
-    cascade_diag_t rec;
-    rec.step = st;
-    rec.t = (double)st * d.dt;
-    rec.E_mean = r[0] / d.nx;
-    rec.J_mean = r[1] / d.nx;
-    rec.E_absmax = r[2];
-    rec.U_E = r[3];
-    rec.U_K = d.w * gs[0];
-    const long long nph = ctl->ph_tail - ctl->ph_head;
-    rec.U_gamma = (double)nph * d.w * d.eps_gamma;
-    rec.gauss_resid = __longlong_as_double(0x7ff8000000000000LL);
-    rec.n_elec = ctl->n[0];
-    rec.n_posi = ctl->n[1];
-    rec.n_photon = nph;
-    rec.n_pairs_total = ctl->pairs_total;
-    rec.n_emit_multi = ctl->emit_multi;
-    d.ring[(st - 1) % d.ring_n] = rec;
+    finish_step(d, r, gs[0]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched cascades.  Per step: conversion for every member (one row of CTAs
+// per member), a one-CTA plan that cuts every member's particles into work
+// items, the persistent particle kernel that hands items out dynamically
+// (each item stages its own member's E and accumulates its current in shared
+// memory, then adds it to the member's FP64 current with global atomics),
+// and the field kernel (one CTA per member).  Members whose remaining step
+// count is zero are skipped by all four.
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void k_batch_convert(BatchDev b) {
+  const int slot = blockIdx.y;
+  if (b.remaining[slot] <= 0) return;
+  const Dev& d = b.devs[slot];
+  Ctl* ctl = d.ctl;
+  const long long step = ctl->step;
+  const long long src = step - 1 - d.n_pp;
+  const long long head = ctl->ph_head;
+  const long long end = (src >= 0) ? d.emit_end[src % (d.n_pp + 1)] : head;
+  const long long n0 = ctl->n[0], n1 = ctl->n[1];
+  long long cnt = end - head;
+  const long long room = min(d.cap - n0, d.cap - n1);
+  const bool over = cnt > room;
+  if (over) cnt = room;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->conv_count = cnt;
+    ctl->conv_end = end;
+    if (over) set_error(ctl, CASCADE_ERR_CAPACITY);
+  }
+  const Real up = (Real)d.u_pair;
+  const Real* ph_off = static_cast<const Real*>(d.ph_off);
+  Real* off0 = static_cast<Real*>(d.off[0]);
+  Real* off1 = static_cast<Real*>(d.off[1]);
+  Real* u0 = static_cast<Real*>(d.u[0]);
+  Real* u1 = static_cast<Real*>(d.u[1]);
+  const long long mask = d.ph_cap - 1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long slot_ph = (head + i) & mask;
+    const int enc = d.ph_cell[slot_ph];
+    const int cell = enc & 0x7fffffff;
+    const Real oc = ph_off[slot_ph];
+    const Real uv = (enc < 0) ? -up : up;
+    d.cell[0][n0 + i] = cell;
+    off0[n0 + i] = oc;
+    u0[n0 + i] = uv;
+    d.cell[1][n1 + i] = cell;
+    off1[n1 + i] = oc;
+    u1[n1 + i] = uv;
+  }
+}
+
+// Work items of every active member (exclusive scan over the slots).
+template <class Real>
+__global__ void __launch_bounds__(1024) k_batch_plan(BatchDev b) {
+  __shared__ long long warp_tot[32];
+  const int per = (b.n + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * per;
+  const int hi = min(lo + per, b.n);
+  long long mine = 0;
+  for (int i = lo; i < hi; ++i) {
+    if (b.remaining[i] > 0) {
+      const Dev& d = b.devs[i];
+      const long long cc = d.ctl->conv_count;
+      const long long P = d.item_size;
+      mine += (d.ctl->n[0] + cc + P - 1) / P + (d.ctl->n[1] + cc + P - 1) / P;
+    }
+  }
+  // block-wide exclusive scan of the per-thread totals
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    long long v = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+    long long w = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long t = __shfl_up_sync(kFull, w, o);
+      if (lane >= o) w += t;
+    }
+    warp_tot[lane] = w - v;  // exclusive prefix of the warps
+  }
+  __syncthreads();
+  long long start = warp_tot[warp] + incl - mine;
+  for (int i = lo; i < hi; ++i) {
+    b.item_start[i] = start;
+    if (b.remaining[i] > 0) {
+      const Dev& d = b.devs[i];
+      const long long cc = d.ctl->conv_count;
+      const long long P = d.item_size;
+      start += (d.ctl->n[0] + cc + P - 1) / P + (d.ctl->n[1] + cc + P - 1) / P;
+    }
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    b.item_start[b.n] = warp_tot[warp] + incl;
+    *b.work_next = 0ull;
+  }
+}
+
+template <class Real, int DEP>
+__global__ void __launch_bounds__(512, 2) k_batch_push(BatchDev b) {
+  typedef typename AccOf<Real, DEP>::type Acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) Dev sd;
+  __shared__ double red[16];
+  __shared__ long long s_item;
+  __shared__ int s_slot;
+  const long long total = b.item_start[b.n];
+  const size_t eb = ((size_t)b.max_nx * sizeof(Real) + 15) & ~size_t(15);
+  PushState<Real, DEP> st;
+  st.Es = reinterpret_cast<Real*>(smem_raw);
+  st.Ss = reinterpret_cast<Acc*>(smem_raw + eb);
+  st.Ls = reinterpret_cast<int*>(smem_raw + 2 * eb);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  while (true) {
+    if (threadIdx.x == 0) {
+      const long long item = (long long)atomicAdd(b.work_next, 1ull);
+      s_item = item;
+      if (item < total) {
+        int lo = 0, hi = b.n;  // last slot with item_start <= item
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (b.item_start[mid] <= item) lo = mid;
+          else hi = mid;
+        }
+        s_slot = lo;
+      }
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= total) break;
+    const int slot = s_slot;
+    {
+      const long long* src = reinterpret_cast<const long long*>(b.devs + slot);
+      long long* dst = reinterpret_cast<long long*>(&sd);
+      for (int w = threadIdx.x; w < (int)(sizeof(Dev) / 8); w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    const Dev& d = sd;
+    Ctl* ctl = d.ctl;
+    const long long cc = ctl->conv_count;
+    const long long N0 = ctl->n[0] + cc, N1 = ctl->n[1] + cc;
+    const long long P = d.item_size;
+    const long long items0 = (N0 + P - 1) / P;
+    const long long local = item - b.item_start[slot];
+    const int s = local < items0 ? 0 : 1;
+    const long long idx = s ? local - items0 : local;
+    const long long Ns = s ? N1 : N0;
+    const long long p0 = idx * P;
+    const long long p1 = min(p0 + P, Ns);
+    const long long c0 = p0 >> 2, c1 = (p1 + 3) >> 2;  // 4-particle chunks
+
+    const int nx = d.nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      st.Es[i] = (Real)d.E[i];
+      st.Ss[i] = Acc(0);
+      if (DEP == 4) st.Ls[i] = 0;
+    }
+    st.ctl = ctl;
+    st.ph_tail = ctl->ph_tail;
+    st.room = d.ph_cap - (st.ph_tail - ctl->conv_end);
+    st.ph_mask = d.ph_cap - 1;
+    set_scales<Real, DEP>(st, (double)(p1 - p0), d.dtdx);
+    __syncthreads();
+
+    double gsum = 0.0;
+    const long long nchunks = c1 - c0;
+    const long long iters = (nchunks + blockDim.x - 1) / blockDim.x;
+    for (long long it = 0; it < iters; ++it) {
+      const long long ch = c0 + it * blockDim.x + warp * 32 + lane;
+      long long base = 0;
+      int cnt = 0;
+      if (ch < c1) {
+        base = ch * 4;
+        cnt = (int)min(4LL, p1 - base);
+      }
+      gsum += (double)process4<Real, kSmemESmemS, DEP, true>(d, st, s, base, cnt, lane);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gsum += __shfl_down_sync(kFull, gsum, o);
+    if (lane == 0) red[warp] = gsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+      atomicAdd(d.uk_part, v);
+    }
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      double v;
+      if (DEP == 1) v = (double)st.Ss[i] * (double)st.fx_inv;
+      else if (DEP == 4) v = (double)st.Ss[i] * (double)st.fx_inv + (double)st.Ls[i] * (double)st.lo_inv;
+      else v = (double)st.Ss[i];
+      if (v != 0.0) atomicAdd(d.S_glob + i, v);
+    }
+    __syncthreads();
+  }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(kFieldBlock) k_batch_field(BatchDev b) {
+  __shared__ double sh[128];
+  const int slot = blockIdx.x;
+  if (b.remaining[slot] <= 0) return;
+  const Dev& d = b.devs[slot];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < d.nx; i += blockDim.x) {
+    const double S = d.S_glob[i];
+    d.S_glob[i] = 0.0;
+    const double J = d.jscale * S;
+    const double E = d.E[i] - d.dt * J;
+    d.E[i] = E;
+    d.J[i] = J;
+    v[0] += E;
+    v[1] += J;
+    v[2] = fmax(v[2], fabs(E));
+    v[3] += 0.5 * E * E * d.dx;
+  }
+  block_reduce4(v, sh);
+  if (threadIdx.x == 0) {
+    const double gsum = *d.uk_part;
+    *d.uk_part = 0.0;
+    finish_step(d, v, gsum);
+    b.remaining[slot] -= 1;
   }
 }
 
@@ -833,6 +1102,46 @@ struct Launchers {
     return cudaGetLastError();
   }
 
+  static const void* batch_push_fn(int dep) {
+    if constexpr (sizeof(Real) == 8) {
+      return reinterpret_cast<const void*>(&k_batch_push<Real, 0>);
+    } else {
+      return dep == 4 ? reinterpret_cast<const void*>(&k_batch_push<Real, 4>)
+                      : reinterpret_cast<const void*>(&k_batch_push<Real, 1>);
+    }
+  }
+
+  static cudaError_t batch_configure(int max_nx, int fine, int num_sms, int* grid, int* block, size_t* smem,
+                                     int* dep) {
+    int dp = sizeof(Real) == 8 ? 0 : (fine ? 4 : 1);
+    const size_t limit = 200 * 1024;
+    if (smem_bytes(max_nx, kSmemESmemS, dp) > limit && dp == 4) dp = 1;
+    const size_t sm = smem_bytes(max_nx, kSmemESmemS, dp);
+    if (sm > limit) return cudaErrorInvalidValue;
+    const void* fn = batch_push_fn(dp);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, sm);
+    if (e != cudaSuccess) return e;
+    *grid = (per_sm < 1 ? 1 : per_sm) * num_sms;
+    *block = 512;
+    *smem = sm;
+    *dep = dp;
+    return cudaSuccess;
+  }
+
+  static cudaError_t batch_step(const BatchDev& b, int grid, int block, size_t smem, int dep, cudaStream_t st) {
+    k_batch_convert<Real><<<dim3(16, b.n), 256, 0, st>>>(b);
+    k_batch_plan<Real><<<1, 1024, 0, st>>>(b);
+    BatchDev arg = b;
+    void* args[] = {&arg};
+    cudaError_t e = cudaLaunchKernel(batch_push_fn(dep), dim3(grid), dim3(block), args, smem, st);
+    if (e != cudaSuccess) return e;
+    k_batch_field<Real><<<b.n, kFieldBlock, 0, st>>>(b);
+    return cudaGetLastError();
+  }
+
   static cudaError_t gauss(const Dev& d, double* rho_dx, double* out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(rho_dx, 0, sizeof(double) * d.nx, st);
     if (e != cudaSuccess) return e;
@@ -858,5 +1167,13 @@ struct Launchers {
     return Launchers<REAL>::gauss(d, rho_dx, out, s);                                        \
   }                                                                                               \
   cudaError_t configure_##SUFFIX(Dev& d, int num_sms) { return Launchers<REAL>::configure(d, num_sms); } \
+  cudaError_t batch_configure_##SUFFIX(int max_nx, int fine, int num_sms, int* grid, int* block,   \
+                                       size_t* smem, int* dep) {                                \
+    return Launchers<REAL>::batch_configure(max_nx, fine, num_sms, grid, block, smem, dep);       \
+  }                                                                                               \
+  cudaError_t batch_step_##SUFFIX(const BatchDev& b, int grid, int block, size_t smem, int dep,   \
+                                  cudaStream_t s) {                                               \
+    return Launchers<REAL>::batch_step(b, grid, block, smem, dep, s);                             \
+  }                                                                                               \
   size_t partial_bytes_##SUFFIX() { return sizeof(REAL); }                                         \
   }
