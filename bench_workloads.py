@@ -25,6 +25,8 @@ def _fp64_one_at_a_time(params: list, steps_of) -> dict:
     from paper_2012_05587_gb300 import Cascade
 
     ps_total, t_total, times = 0.0, 0.0, []
+    if not params:
+        return {"value": None, "unit": UNIT, "cascades": 0, "seconds": 0.0, "per_request_s": [0.0]}
     for p in params:
         q = dict(p, precision="fp64")
         torch.cuda.synchronize()
@@ -85,7 +87,7 @@ def run_batch(args) -> int:
                    "members_over_capacity": over, "create_s": t_create, "wall_s": wall},
         "fp64_one_at_a_time": dict(fp64, per_request_s=None,
                                    sample=f"first {args.fp64_sample} cascades of the scan, each alone in FP64"),
-        "batched_over_fp64_one_at_a_time": value / fp64["value"],
+        "batched_over_fp64_one_at_a_time": value / fp64["value"] if fp64["value"] else None,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -158,7 +160,7 @@ def run_serve(args) -> int:
         "fp64_alone": dict(fp64, p50_s=float(np.percentile(fp64["per_request_s"], 50)),
                            p99_s=float(np.percentile(fp64["per_request_s"], 99)), per_request_s=None,
                            sample=f"first {args.fp64_sample} requests, each alone in FP64"),
-        "served_over_fp64_alone": (ps / wall) / fp64["value"],
+        "served_over_fp64_alone": (ps / wall) / fp64["value"] if fp64["value"] else None,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -217,8 +218,12 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
     if (!d.S_glob) return CASCADE_ERR_OOM;
   }
   {
-    long long it = 4LL * d.nx;
-    if (it < 8192) it = 8192;
+    // batched work item: enough particles that staging E and flushing the
+    // current (about 2 nx words each) stay a small part of the item's work
+    const char* env = getenv("CASCADE_BATCH_ITEM_MULT");
+    const long long mult = (env && *env) ? atoll(env) : 16;
+    long long it = (mult > 0 ? mult : 16) * (long long)d.nx;
+    if (it < 16384) it = 16384;
     d.item_size = (it + 3) & ~3LL;
   }
   d.uk_part = static_cast<double*>(h->dalloc(sizeof(double) * d.grid_push));
@@ -249,30 +254,44 @@ int upload_E(cascade_t* h, const double* E_host) {
   return CASCADE_OK;
 }
 
+// Copy one species from host arrays: cells straight into place, offsets and
+// momenta through a device staging buffer in chunks; a kernel rounds them to
+// the particle precision and checks every particle.
 int upload_species(cascade_t* h, int s, long long n, const int32_t* cell, const double* off, const double* u) {
   if (n == 0) return CASCADE_OK;
-  for (long long i = 0; i < n; ++i) {
-    if (cell[i] < 0 || cell[i] >= h->p.nx || !(off[i] >= 0.0) || !(off[i] < 1.0) || !isfinite(u[i])) {
-      snprintf(g_msg, sizeof(g_msg), "particle %lld of species %d outside the grid or not finite", i, s);
-      return CASCADE_ERR_INVALID_ARG;
-    }
+  const long long chunk = n < (1LL << 23) ? n : (1LL << 23);
+  const size_t stage_bytes = sizeof(double) * (size_t)chunk;
+  void* stage = nullptr;
+  if (h->alloc_fn) {
+    stage = h->alloc_fn(2 * stage_bytes, (void*)h->stream, h->alloc_ctx);
+  } else if (cudaMalloc(&stage, 2 * stage_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    stage = nullptr;
   }
-  CUDA_TRY(cudaMemcpyAsync(h->d.cell[s], cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
-  if (h->real_size == sizeof(double)) {
-    CUDA_TRY(cudaMemcpyAsync(h->d.off[s], off, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(h->d.u[s], u, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(cudaStreamSynchronize(h->stream));
-  } else {
-    std::vector<float> fo(n), fu(n);
-    for (long long i = 0; i < n; ++i) {
-      float o = (float)off[i];
-      if (o >= 1.0f) o = 0x1.fffffep-1f;  // keep the offset inside the cell
-      fo[i] = o;
-      fu[i] = (float)u[i];
-    }
-    CUDA_TRY(cudaMemcpyAsync(h->d.off[s], fo.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(h->d.u[s], fu.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (!stage) return CASCADE_ERR_OOM;
+  double* so = static_cast<double*>(stage);
+  double* su = so + chunk;
+  unsigned int* bad = reinterpret_cast<unsigned int*>(h->scalar);
+  unsigned int nbad = 0;
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d.cell[s], cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream);
+  for (long long k = 0; k < n && e == cudaSuccess; k += chunk) {
+    const long long m = (n - k) < chunk ? (n - k) : chunk;
+    e = cudaMemcpyAsync(so, off + k, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(su, u + k, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = h->real_size == sizeof(double) ? upload_fp64(h->d, s, k, m, so, su, bad, h->stream)
+                                         : upload_fp32(h->d, s, k, m, so, su, bad, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (h->free_fn) h->free_fn(stage, (void*)h->stream, h->alloc_ctx);
+  else cudaFree(stage);
+  if (e != cudaSuccess) return cuda_fail(e, "state upload");
+  if (nbad) {
+    snprintf(g_msg, sizeof(g_msg), "%u particles of species %d outside the grid or not finite", nbad, s);
+    return CASCADE_ERR_INVALID_ARG;
   }
   return CASCADE_OK;
 }

@@ -101,7 +101,9 @@ void set_error_message(const char* msg);
                                        size_t* smem, int* dep);                                 \
   cudaError_t batch_step_##SUFFIX(const BatchDev& b, int grid, int block, size_t smem, int dep,   \
                                   cudaStream_t s);                                              \
-  size_t partial_bytes_##SUFFIX();
+  size_t partial_bytes_##SUFFIX();                                                             \
+  cudaError_t upload_##SUFFIX(const Dev& d, int sp, long long first, long long count, const double* off_src, \
+                              const double* u_src, unsigned int* bad, cudaStream_t s);
 
 CASCADE_DECLARE_LAUNCHERS(fp64)
 CASCADE_DECLARE_LAUNCHERS(fp32)

@@ -23,6 +23,7 @@
 namespace cpic {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kFieldGroups = 8;  // row groups of the field kernel (kFieldBlock / 32)
 // Upper bound on photons one lepton emits in one step (a step that needs more
 // is far too coarse for the model; the count is clamped).
 constexpr int kMaxPhotonsPerStep = 1 << 16;
@@ -657,29 +658,32 @@ __device__ __forceinline__ void finish_step(const Dev& d, const double r[4], dou
 
 template <class Acc, bool kPartials>
 __global__ void __launch_bounds__(kFieldBlock) k_field(Dev d) {
+  // 32 edges per CTA; the 8 warps each sum every 8th per-CTA partial row of
+  // those edges (coalesced), then warp 0 adds the 8 group sums in order, so
+  // the FP64 sum over rows has a fixed order
   __shared__ double sh[128];
+  __shared__ double grp[kFieldGroups][32];
   __shared__ int s_last;
   Ctl* ctl = d.ctl;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
   const int G = ctl->active_blocks;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  if (i < d.nx) {
+  if (kPartials) {
     double S = 0.0;
-    if (kPartials) {
+    if (i < d.nx) {
       const Acc* P = static_cast<const Acc*>(d.S_part) + i;
       const size_t pitch = d.nxp;
-      int b = 0;
-      for (; b + 4 <= G; b += 4) {
-        const double s0 = (double)P[(size_t)b * pitch];
-        const double s1 = (double)P[(size_t)(b + 1) * pitch];
-        const double s2 = (double)P[(size_t)(b + 2) * pitch];
-        const double s3 = (double)P[(size_t)(b + 3) * pitch];
-        S += s0;
-        S += s1;
-        S += s2;
-        S += s3;
-      }
-      for (; b < G; ++b) S += (double)P[(size_t)b * pitch];
+      for (int b = g; b < G; b += kFieldGroups) S += (double)P[(size_t)b * pitch];
+    }
+    grp[g][lane] = S;
+    __syncthreads();
+  }
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (g == 0 && i < d.nx) {
+    double S = 0.0;
+    if (kPartials) {
+#pragma unroll
+      for (int k = 0; k < kFieldGroups; ++k) S += grp[k][lane];
     } else {
       S = d.S_glob[i];
       d.S_glob[i] = 0.0;
@@ -830,8 +834,8 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchDev b) {
   }
 }
 
-template <class Real, int DEP>
-__global__ void __launch_bounds__(512, 2) k_batch_push(BatchDev b) {
+template <class Real, int DEP, int MINB>
+__global__ void __launch_bounds__(512, MINB) k_batch_push(BatchDev b) {
   typedef typename AccOf<Real, DEP>::type Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) Dev sd;
@@ -958,6 +962,35 @@ __global__ void __launch_bounds__(kFieldBlock) k_batch_field(BatchDev b) {
 }
 
 // ---------------------------------------------------------------------------
+// Upload of a caller's state: offsets and momenta arrive as FP64 in a staging
+// buffer and are rounded to the particle precision (an offset that rounds up
+// to 1 is kept just below it); every particle is checked (cell inside the
+// grid, offset in [0, 1), finite momentum) and the number of bad ones is
+// counted in *bad.
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void k_upload(Dev d, int s, long long first, long long count, const double* off_src,
+                         const double* u_src, unsigned int* bad) {
+  Real* off = static_cast<Real*>(d.off[s]) + first;
+  Real* u = static_cast<Real*>(d.u[s]) + first;
+  const int* cell = d.cell[s] + first;
+  unsigned int nbad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double o = off_src[i];
+    const double uu = u_src[i];
+    const int c = cell[i];
+    const bool ok = c >= 0 && c < d.nx && o >= 0.0 && o < 1.0 && isfinite(uu);
+    Real oo = (Real)o;
+    if (!(oo < Real(1))) oo = Real(1) - (sizeof(Real) == 4 ? Real(5.9604645e-8) : Real(1.1102230246251565e-16));
+    off[i] = ok ? oo : Real(0);
+    u[i] = ok ? (Real)uu : Real(0);
+    nbad += ok ? 0u : 1u;
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+// ---------------------------------------------------------------------------
 // Gauss's-law residual of the current state (diagnostic, not in the step).
 // ---------------------------------------------------------------------------
 template <class Real>
@@ -1067,7 +1100,7 @@ struct Launchers {
     if (per_sm < 1) per_sm = 1;
     d.block_push = block;
     d.grid_push = per_sm * num_sms;
-    d.grid_field = (d.nx + kFieldBlock - 1) / kFieldBlock;
+    d.grid_field = (d.nx + 31) / 32;
     d.nxp = (d.nx + 31) & ~31;
     d.min_per_cta = d.nx > 2048 ? d.nx : 2048;
     return cudaSuccess;
@@ -1102,12 +1135,18 @@ struct Launchers {
     return cudaGetLastError();
   }
 
-  static const void* batch_push_fn(int dep) {
+  // minb: CTAs per SM the register budget is sized for (1: up to 128
+  // registers, no spills; 2: 64 registers)
+  static const void* batch_push_fn(int dep, int minb) {
     if constexpr (sizeof(Real) == 8) {
-      return reinterpret_cast<const void*>(&k_batch_push<Real, 0>);
+      return minb == 2 ? reinterpret_cast<const void*>(&k_batch_push<Real, 0, 2>)
+                       : reinterpret_cast<const void*>(&k_batch_push<Real, 0, 1>);
     } else {
-      return dep == 4 ? reinterpret_cast<const void*>(&k_batch_push<Real, 4>)
-                      : reinterpret_cast<const void*>(&k_batch_push<Real, 1>);
+      if (dep == 4)
+        return minb == 2 ? reinterpret_cast<const void*>(&k_batch_push<Real, 4, 2>)
+                         : reinterpret_cast<const void*>(&k_batch_push<Real, 4, 1>);
+      return minb == 2 ? reinterpret_cast<const void*>(&k_batch_push<Real, 1, 2>)
+                       : reinterpret_cast<const void*>(&k_batch_push<Real, 1, 1>);
     }
   }
 
@@ -1118,7 +1157,8 @@ struct Launchers {
     if (smem_bytes(max_nx, kSmemESmemS, dp) > limit && dp == 4) dp = 1;
     const size_t sm = smem_bytes(max_nx, kSmemESmemS, dp);
     if (sm > limit) return cudaErrorInvalidValue;
-    const void* fn = batch_push_fn(dp);
+    const int minb = env_int("CASCADE_BATCH_MINB", 1) == 2 ? 2 : 1;
+    const void* fn = batch_push_fn(dp, minb);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -1127,7 +1167,7 @@ struct Launchers {
     *grid = (per_sm < 1 ? 1 : per_sm) * num_sms;
     *block = 512;
     *smem = sm;
-    *dep = dp;
+    *dep = dp + 16 * minb;  // kernel selector: accumulator form and register budget
     return cudaSuccess;
   }
 
@@ -1136,9 +1176,18 @@ struct Launchers {
     k_batch_plan<Real><<<1, 1024, 0, st>>>(b);
     BatchDev arg = b;
     void* args[] = {&arg};
-    cudaError_t e = cudaLaunchKernel(batch_push_fn(dep), dim3(grid), dim3(block), args, smem, st);
+    cudaError_t e = cudaLaunchKernel(batch_push_fn(dep % 16, dep / 16), dim3(grid), dim3(block), args, smem, st);
     if (e != cudaSuccess) return e;
     k_batch_field<Real><<<b.n, kFieldBlock, 0, st>>>(b);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t upload(const Dev& d, int sp, long long first, long long count, const double* off_src,
+                            const double* u_src, unsigned int* bad, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_upload<Real><<<(int)blocks, 256, 0, st>>>(d, sp, first, count, off_src, u_src, bad);
     return cudaGetLastError();
   }
 
@@ -1175,5 +1224,9 @@ struct Launchers {
                                   cudaStream_t s) {                                               \
     return Launchers<REAL>::batch_step(b, grid, block, smem, dep, s);                             \
   }                                                                                               \
-  size_t partial_bytes_##SUFFIX() { return sizeof(REAL); }                                         \
+  size_t partial_bytes_##SUFFIX() { return sizeof(REAL); }                                       \
+  cudaError_t upload_##SUFFIX(const Dev& d, int sp, long long first, long long count, const double* o, \
+                              const double* u, unsigned int* bad, cudaStream_t s) {               \
+    return Launchers<REAL>::upload(d, sp, first, count, o, u, bad, s);                            \
+  }                                         \
   }

@@ -282,3 +282,15 @@ def test_fine_deposit_is_closer_to_fp64():
         errs[prec] = np.abs(J - J_ref).max() / np.abs(J_ref).max()
     assert errs["fp32_fine"] <= errs["fp32"]
     assert errs["fp32_fine"] < 1e-5
+
+
+def test_state_upload_rejects_particles_outside_the_grid():
+    p = dict(W.small_cascade(), particle_cap=64)
+    bad = {"elec": {"cell": [3, 256], "off": [0.5, 0.5], "u": [0.0, 0.0]},
+           "posi": {"cell": [3], "off": [0.5], "u": [0.0]}}
+    with pytest.raises(CascadeError) as ei:
+        Cascade(p, state=bad)
+    assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
+    nan_u = {"elec": {"cell": [3], "off": [0.5], "u": [float("nan")]}, "posi": {"cell": [3], "off": [0.5], "u": [0.0]}}
+    with pytest.raises(CascadeError):
+        Cascade(dict(p, precision="fp32"), state=nan_u)
