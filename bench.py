@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cap", type=int, default=0, help="particle cap per species (0 = the workload's)")
     ap.add_argument("--ppc", type=int, default=0, help="seed particles per cell per species (0 = the workload's)")
-    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "sweep"],
+    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "sweep", "paper"],
                     help="large: one large cascade (default); batch: the 256-cascade parameter scan in one "
                          "launch per step; serve: Poisson arrivals admitted by footprint; sweep: FP32 vs FP64 "
                          "errors of the ensemble diagnostics")
@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=400)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--fp64-sample", type=int, default=8, help="cascades run one at a time in FP64 for comparison")
+    ap.add_argument("--paper-time", type=float, default=12.0, help="paper workload: simulated time (1/omega_p)")
+    ap.add_argument("--save-series", default="", help="paper workload: directory for the per-step series")
     return ap.parse_args()
 
 
@@ -151,6 +153,22 @@ def oracle_slice(steps_prep: int, steps_timed: int):
     ps = float((d["n_elec"] + d["n_posi"]).sum())
     return ps / el, ps, el, (f"FP64 oracle, 1 thread, Nx=512 slice of the large cascade (64+64 per cell), "
                              f"steps {steps_prep}-{steps_prep + steps_timed}, {ps:.3g} particle-steps in {el:.1f} s")
+
+
+def aggregate_over_ranks(ms: float, particle_steps: float, device: str = "cuda"):
+    """Whole-job figures of N independent replicas: the slowest rank's time and
+    the particle-steps of all ranks (no data-path exchange: each rank runs its
+    own cascade).  With one rank, the rank's own numbers."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, particle_steps
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    p = torch.tensor([particle_steps], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(p[0])
 
 
 def run_reference(args):
@@ -250,15 +268,7 @@ def main():
     ps = float((rec["n_elec"] + rec["n_posi"]).sum())
     n_now = int(rec["n_elec"][-1] + rec["n_posi"][-1])
 
-    t_max = ms
-    ps_all = ps
-    if world > 1:
-        tt = torch.tensor([ms, ps], dtype=torch.float64, device="cuda")
-        tmax = tt.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_max = float(tmax[0])
-        ps_all = float(tt[1])
+    t_max, ps_all = aggregate_over_ranks(ms, ps, "cuda")
     value = ps_all / (t_max / 1e3)
 
     peak, peak_kind = measured_peak()

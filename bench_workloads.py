@@ -4,6 +4,7 @@ the large-cascade line)."""
 from __future__ import annotations
 
 import json
+import os
 import time
 
 import numpy as np
@@ -199,5 +200,100 @@ def run_sweep(args) -> int:
     return 0
 
 
+def paper_scale_params(f: float, precision: str = "fp32") -> dict:
+    """Section 3 setup at the paper's own parameters: E0 = 10^3.5, L = 10^1.5
+    in N_L = 2000 cells, dt = 10^-3.5, gamma_thr = 500, one particle per cell
+    per species, in-place pair creation (l_pp = 0)."""
+    g = 500.0
+    eps = f * g
+    E0 = 10 ** 3.5
+    nx = 2000
+    pred = E0 * E0 * np.log(2 / f) / (2 * g)  # Eq. 5 screening density per species, in n0
+    return dict(nx=nx, ppc=1, dx=10 ** 1.5 / nx, dt=10 ** -3.5, n0=1.0, u_spread=0.0, seed=9000 + int(1e4 * f),
+                E0=E0, gamma_thr=g, eps_gamma=eps, l_pp=0.0, precision=precision,
+                particle_cap=int(1.5 * pred * nx) + 4096, diag_ring=1 << 16)
+
+
+def run_paper(args) -> int:
+    """The paper-scale cascades of Section 3 (f = 0.1, 0.01, 0.004) against
+    Eq. 3 (growth), Eq. 5 (density at screening), Eq. 10 (mean gamma) and
+    Eq. 12 (oscillation frequency, with the measured n and <1/gamma^3>)."""
+    import torch
+
+    from paper_2012_05587_gb300 import Cascade, analysis as A
+
+    rows = []
+    for f in (0.1, 0.01, 0.004):
+        p = paper_scale_params(f, args.precision)
+        g, eps, E0 = p["gamma_thr"], p["eps_gamma"], p["E0"]
+        ta = g / E0
+        steps = int(args.paper_time / p["dt"])
+        t0 = time.perf_counter()
+        with Cascade(p) as c:
+            # run to the first zero of <E> (screening), chunk by chunk
+            done = 0
+            recs = []
+            while done < steps:
+                c.step(500)
+                done += 500
+                r = c.diag(500)
+                recs.append(r)
+                if (r["E_mean"] <= 0).any():
+                    break
+            cat = {k: np.concatenate([x[k] for x in recs]) for k in recs[0]}
+            st_e, st_p = c.particles(0), c.particles(1)
+            u = np.concatenate([st_e["u"], st_p["u"]])
+            gam = np.sqrt(1.0 + u * u)
+            n_now = len(u) / (2 * p["nx"] * p["ppc"])
+            osc_pred = float(np.sqrt(2 * n_now * np.mean(1.0 / gam ** 3)))
+            # continue through the oscillations
+            c.step(steps - done)
+            r2 = c.diag(steps - done)
+            full = {k: np.concatenate([cat[k], r2[k]]) for k in cat}
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        t = full["t"]
+        N = full["n_elec"] + full["n_posi"]
+        z = A.zero_crossings(t, full["E_mean"])
+        ts = float(z[0]) if len(z) else float("nan")
+        k_s = int(np.searchsorted(t, ts))
+        # growth: N between 10x the seed and a tenth of its value at screening
+        # growth: fit of ln N over the cascade, from 100x the seed to a third
+        # of the count at screening (the cold seed grows in generations, so
+        # the fit spans several of them)
+        lnN = np.log(N.astype(float))
+        m = (N >= 100 * N[0]) & (N <= N[k_s] / 3.0) & (t < ts)
+        G = float(np.polyfit(t[m], lnN[m], 1)[0]) if m.sum() > 5 else float("nan")
+        if args.save_series:
+            np.savez_compressed(os.path.join(args.save_series, f"paper_f{f}.npz"), t=t, N=N, E=full["E_mean"],
+                                UK=full["U_K"], UE=full["U_E"], pairs=full["n_pairs_total"])
+        ns = full["n_elec"][k_s] / (p["nx"] * p["ppc"])
+        L = p["nx"] * p["dx"]
+        row = {
+            "f": f, "steps": steps, "seconds": el,
+            "particle_steps": float(N.sum()),
+            "growth_rate_t_a": G * ta,
+            "eq3_W_2_over_f": A.lambert_growth_rate(E0, g, eps) * ta,
+            "renewal_t_a": A.renewal_growth_rate(E0, g, eps) * ta,
+            "screening_time": ts,
+            "n_s_over_n0": float(ns),
+            "eq5_over_measured": float(A.screening_density(E0, g, eps) / ns),
+            "kinetic_share_at_screening": float((full["U_K"][k_s] - full["U_K"][0]) / (0.5 * E0 ** 2 * L)),
+            "mean_gamma_at_screening": float(gam.mean()),
+            "eq10_mean_gamma": float(A.mean_gamma(g, eps)),
+            "osc_freq_measured": float(np.pi / np.mean(np.diff(z[:6]))) if len(z) > 3 else float("nan"),
+            "eq12_with_measured_n_and_inv_gamma3": osc_pred,
+            "final_pairs": float(full["n_pairs_total"][-1]),
+            "mean_E_envelope_last_over_first": float(np.abs(full["E_mean"][t > ts]).max() and
+                                                     np.abs(full["E_mean"][-len(t) // 10:]).max() /
+                                                     np.abs(full["E_mean"][t > ts]).max()),
+        }
+        rows.append(row)
+        print(json.dumps({"paper_row": row}), flush=True)
+    print(json.dumps({"metric": B.METRIC, "value": None, "unit": UNIT, "workload": "paper-scale cascades",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def run(args) -> int:
-    return {"batch": run_batch, "serve": run_serve, "sweep": run_sweep}[args.workload](args)
+    return {"batch": run_batch, "serve": run_serve, "sweep": run_sweep, "paper": run_paper}[args.workload](args)

@@ -162,6 +162,14 @@ int cascade_gauss(cascade_t* h, double* resid_out);
 /* Synchronise and copy particle counts, photons in flight and the step index. */
 int cascade_counts(cascade_t* h, int64_t* n_elec, int64_t* n_posi, int64_t* n_photon, int64_t* step);
 
+/* Phase-space histogram of one species (Fig. 2 and Eq. 8 of the paper show
+ * these distributions): quantity 0 = momentum u, 1 = Lorentz factor gamma,
+ * 2 = position x (in units of c/omega_p).  nbins (1 .. 65536) equal bins over
+ * [lo, hi); values outside are not counted.  counts_host receives nbins
+ * counts.  Synchronises the stream. */
+int cascade_histogram(cascade_t* h, int32_t species, int32_t quantity, int32_t nbins, double lo, double hi,
+                      int64_t* counts_host);
+
 /* Synchronise and copy up to max particles of one species (0 = electrons,
  * 1 = positrons) in storage order into host arrays (nullable each); n_out
  * gets the number copied. */

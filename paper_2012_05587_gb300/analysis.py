@@ -58,3 +58,38 @@ def relative_errors(a: dict, ref: dict) -> dict:
         x = a.get(k, float("nan"))
         out[k] = float(abs(x - v) / abs(v)) if v not in (0.0,) and np.isfinite(v) and np.isfinite(x) else float("nan")
     return out
+
+
+# --- closed forms of the model (Sections 3-5) ------------------------------------
+
+def lambert_growth_rate(E0: float, gamma_thr: float, eps_gamma: float) -> float:
+    """Eq. 3: Gamma t_a = W(2/f), t_a = gamma_thr / E0."""
+    from scipy.special import lambertw
+
+    f = eps_gamma / gamma_thr
+    return float(lambertw(2.0 / f).real) * E0 / gamma_thr
+
+
+def renewal_growth_rate(E0: float, gamma_thr: float, eps_gamma: float, delay: float = 0.0) -> float:
+    """Growth rate of the threshold cascade in a uniform, unscreened field:
+    exp(-G (T2 + d)) + exp(-G (T3 + d)) = 1 - exp(-G T1), with T1 the
+    re-emission time of a lepton at threshold and T2, T3 the times for a new
+    pair member to reach threshold along and against the field."""
+    from scipy.optimize import brentq
+
+    ut = np.sqrt(gamma_thr ** 2 - 1.0)
+    ur = np.sqrt((gamma_thr - eps_gamma) ** 2 - 1.0)
+    up = np.sqrt((eps_gamma / 2.0) ** 2 - 1.0)
+    T1, T2, T3 = (ut - ur) / E0, (ut - up) / E0, (ut + up) / E0
+    return float(brentq(lambda G: np.exp(-G * (T2 + delay)) + np.exp(-G * (T3 + delay)) - (1 - np.exp(-G * T1)),
+                        1e-9 / T1, 50.0 / T1))
+
+
+def screening_density(E0: float, gamma_thr: float, eps_gamma: float) -> float:
+    """Eq. 5 in units of n0."""
+    return E0 * E0 * np.log(2.0 * gamma_thr / eps_gamma) / (2.0 * gamma_thr)
+
+
+def mean_gamma(gamma_thr: float, eps_gamma: float) -> float:
+    """Eq. 10: <gamma> = gamma_thr / ln(2/f)."""
+    return gamma_thr / np.log(2.0 * gamma_thr / eps_gamma)

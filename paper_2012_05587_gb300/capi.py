@@ -97,6 +97,7 @@ def load() -> ctypes.CDLL:
             "cascade_gauss": ([vp, P(f64)], ctypes.c_int),
             "cascade_counts": ([vp, P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
             "cascade_particles": ([vp, i32, i64, vp, vp, vp, P(i64)], ctypes.c_int),
+            "cascade_histogram": ([vp, i32, i32, i32, f64, f64, vp], ctypes.c_int),
             "cascade_destroy": ([vp], ctypes.c_int),
             "cascade_footprint": ([P(cascade_params), P(i32), P(ctypes.c_size_t)], ctypes.c_int),
             "cascade_set_timing": ([vp, i32], ctypes.c_int),
@@ -255,6 +256,16 @@ def cascade_particles(h, species: int, max_n: int) -> dict:
                                                         _ptr(u), ctypes.byref(n)))
     k = n.value
     return {"cell": cell[:k], "off": off[:k], "u": u[:k]}
+
+
+HIST_U, HIST_GAMMA, HIST_X = 0, 1, 2
+
+
+def cascade_histogram(h, species: int, quantity: int, nbins: int, lo: float, hi: float) -> np.ndarray:
+    out = np.zeros(nbins, np.int64)
+    check("cascade_histogram", load().cascade_histogram(h, int(species), int(quantity), int(nbins), float(lo),
+                                                        float(hi), out.ctypes.data))
+    return out
 
 
 def cascade_destroy(h) -> None:

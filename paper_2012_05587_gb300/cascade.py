@@ -58,6 +58,10 @@ class Cascade:
         n = c["n_elec"] if species == 0 else c["n_posi"]
         return capi.cascade_particles(self.h, species, n)
 
+    def histogram(self, species: int, quantity: str, nbins: int, lo: float, hi: float) -> np.ndarray:
+        q = {"u": capi.HIST_U, "gamma": capi.HIST_GAMMA, "x": capi.HIST_X}[quantity]
+        return capi.cascade_histogram(self.h, species, q, nbins, lo, hi)
+
     def close(self) -> None:
         if getattr(self, "h", None):
             capi.cascade_destroy(self.h)

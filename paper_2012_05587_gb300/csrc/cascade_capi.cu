@@ -208,7 +208,7 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
   d.E = static_cast<double*>(h->dalloc(sizeof(double) * d.nx));
   d.J = static_cast<double*>(h->dalloc(sizeof(double) * d.nx));
   const size_t acc = params->precision == CASCADE_FP64 ? partial_bytes_fp64() : partial_bytes_fp32();
-  if (d.variant == kSmemESmemS && !batch_member) {
+  if ((d.variant == kSmemESmemS || d.variant == kGlobESmemS) && !batch_member) {
     d.S_part = h->dalloc(acc * (size_t)d.grid_push * d.nxp);
     if (!d.S_part) return CASCADE_ERR_OOM;
   } else {
@@ -221,8 +221,8 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
     // batched work item: enough particles that staging E and flushing the
     // current (about 2 nx words each) stay a small part of the item's work
     const char* env = getenv("CASCADE_BATCH_ITEM_MULT");
-    const long long mult = (env && *env) ? atoll(env) : 16;
-    long long it = (mult > 0 ? mult : 16) * (long long)d.nx;
+    const long long mult = (env && *env) ? atoll(env) : 64;
+    long long it = (mult > 0 ? mult : 64) * (long long)d.nx;
     if (it < 16384) it = 16384;
     d.item_size = (it + 3) & ~3LL;
   }
@@ -478,6 +478,29 @@ int cascade_counts(cascade_t* h, int64_t* n_elec, int64_t* n_posi, int64_t* n_ph
   if (n_posi) *n_posi = c.n[1];
   if (n_photon) *n_photon = c.ph_tail - c.ph_head;
   if (step) *step = c.step;
+  return h->sticky;
+}
+
+int cascade_histogram(cascade_t* h, int32_t species, int32_t quantity, int32_t nbins, double lo, double hi,
+                      int64_t* counts_host) {
+  if (!h || species < 0 || species > 1 || quantity < 0 || quantity > 2 || nbins < 1 || nbins > 65536 ||
+      !(hi > lo) || !counts_host)
+    return CASCADE_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  void* buf = nullptr;
+  const size_t bytes = sizeof(unsigned long long) * (size_t)nbins;
+  if (h->alloc_fn) buf = h->alloc_fn(bytes, (void*)h->stream, h->alloc_ctx);
+  else if (cudaMalloc(&buf, bytes) != cudaSuccess) buf = nullptr;
+  if (!buf) return CASCADE_ERR_OOM;
+  unsigned long long* out = static_cast<unsigned long long*>(buf);
+  cudaError_t e = h->real_size == sizeof(double)
+                      ? histogram_fp64(h->d, species, quantity, nbins, lo, hi, out, h->stream)
+                      : histogram_fp32(h->d, species, quantity, nbins, lo, hi, out, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(counts_host, out, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (h->free_fn) h->free_fn(buf, (void*)h->stream, h->alloc_ctx);
+  else cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "histogram");
   return h->sticky;
 }
 

@@ -81,6 +81,7 @@ enum PushVariant {
   kSmemESmemS = 0,  // E and the charge-flux accumulator in shared memory
   kSmemEGlobS = 1,  // E in shared memory, flux through global FP64 atomics
   kGlobEGlobS = 2,  // both in global memory (very large grids)
+  kGlobESmemS = 3,  // E read through L1 from global memory, accumulator in shared memory
 };
 
 constexpr int kFieldBlock = 256;
@@ -102,6 +103,8 @@ void set_error_message(const char* msg);
   cudaError_t batch_step_##SUFFIX(const BatchDev& b, int grid, int block, size_t smem, int dep,   \
                                   cudaStream_t s);                                              \
   size_t partial_bytes_##SUFFIX();                                                             \
+  cudaError_t histogram_##SUFFIX(const Dev& d, int sp, int quantity, int nbins, double lo, double hi,    \
+                                 unsigned long long* out, cudaStream_t s);                           \
   cudaError_t upload_##SUFFIX(const Dev& d, int sp, long long first, long long count, const double* off_src, \
                               const double* u_src, unsigned int* bad, cudaStream_t s);
 

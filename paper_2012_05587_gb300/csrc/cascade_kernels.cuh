@@ -295,7 +295,7 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
     const int ib = hi ? ((c + 1 == nx) ? 0 : c + 1) : c;
     const Real w = hi ? o - half : o + half;
     Real Ea, Eb;
-    if (V == kGlobEGlobS) {
+    if (V == kGlobEGlobS || V == kGlobESmemS) {
       Ea = (Real)__ldg(d.E + ia);
       Eb = (Real)__ldg(d.E + ib);
     } else {
@@ -353,7 +353,7 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
   // deposit
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    if (V == kSmemESmemS) {
+    if (V == kSmemESmemS || V == kGlobESmemS) {
       if (DEP == 1) {
         if (e1[j] >= 0) atomicAdd(&st.Ss[e1[j]], __float2int_rn((float)a1[j] * st.fx_scale));
         if (e2[j] >= 0) atomicAdd(&st.Ss[e2[j]], __float2int_rn((float)a2[j] * st.fx_scale));
@@ -505,8 +505,15 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
 // live (see PushVariant).  Persistent grid; the number of working CTAs
 // follows the particle count.
 // ---------------------------------------------------------------------------
+// FP32: 1024 threads (64 registers); FP64 needs more registers per particle,
+// so 512 threads with up to 128 registers and no spills.
+template <class Real>
+struct PushBlock {
+  static constexpr int value = sizeof(Real) == 8 ? 512 : 1024;
+};
+
 template <class Real, int V, int DEP, bool FAST>
-__global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
+__global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
   typedef typename AccOf<Real, DEP>::type Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
@@ -519,12 +526,12 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
   PushState<Real, DEP> st;
   st.ctl = ctl;
   st.Es = reinterpret_cast<Real*>(smem_raw);
-  st.Ss = reinterpret_cast<Acc*>(smem_raw + eb);
+  st.Ss = reinterpret_cast<Acc*>(smem_raw + (V == kGlobESmemS ? 0 : eb));
   st.Ls = reinterpret_cast<int*>(smem_raw + 2 * eb);  // DEP 4 residual word
-  if (V != kGlobEGlobS) {
+  if (V == kSmemESmemS || V == kSmemEGlobS) {
     for (int i = threadIdx.x; i < nx; i += blockDim.x) st.Es[i] = (Real)d.E[i];
   }
-  if (V == kSmemESmemS) {
+  if (V == kSmemESmemS || V == kGlobESmemS) {
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       st.Ss[i] = Acc(0);
       if (DEP == 4) st.Ls[i] = 0;
@@ -570,7 +577,7 @@ __global__ void __launch_bounds__(1024, 1) k_push(Dev d) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     if (lane == 0) d.uk_part[blockIdx.x] = v;
   }
-  if (V == kSmemESmemS) {
+  if (V == kSmemESmemS || V == kGlobESmemS) {
     Real* P = static_cast<Real*>(d.S_part) + (size_t)blockIdx.x * d.nxp;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       if (DEP == 1) P[i] = (Real)((float)st.Ss[i] * st.fx_inv);
@@ -991,6 +998,37 @@ __global__ void k_upload(Dev d, int s, long long first, long long count, const d
 }
 
 // ---------------------------------------------------------------------------
+// Phase-space histogram of one species: per-CTA shared-memory counts, then
+// one global atomic per non-empty bin.
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void k_histogram(Dev d, int s, int quantity, int nbins, double lo, double hi,
+                            unsigned long long* out) {
+  extern __shared__ unsigned int hcount[];
+  for (int i = threadIdx.x; i < nbins; i += blockDim.x) hcount[i] = 0u;
+  __syncthreads();
+  const long long n = d.ctl->n[s];
+  const double scale = nbins / (hi - lo);
+  const Real* off = static_cast<const Real*>(d.off[s]);
+  const Real* u = static_cast<const Real*>(d.u[s]);
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    double v;
+    if (quantity == 0) v = (double)u[p];
+    else if (quantity == 1) v = sqrt(1.0 + (double)u[p] * (double)u[p]);
+    else v = ((double)d.cell[s][p] + (double)off[p]) * d.dx;
+    if (v >= lo && v < hi) {
+      int b = (int)((v - lo) * scale);
+      b = b >= nbins ? nbins - 1 : b;
+      atomicAdd(&hcount[b], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nbins; i += blockDim.x)
+    if (hcount[i]) atomicAdd(out + i, (unsigned long long)hcount[i]);
+}
+
+// ---------------------------------------------------------------------------
 // Gauss's-law residual of the current state (diagnostic, not in the step).
 // ---------------------------------------------------------------------------
 template <class Real>
@@ -1040,6 +1078,7 @@ template <>
 inline const void* PushTable<double>::get(int V, int, bool) {
   if (V == kSmemESmemS) return reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false>);
   if (V == kSmemEGlobS) return reinterpret_cast<const void*>(&k_push<double, kSmemEGlobS, 0, false>);
+  if (V == kGlobESmemS) return reinterpret_cast<const void*>(&k_push<double, kGlobESmemS, 0, false>);
   return reinterpret_cast<const void*>(&k_push<double, kGlobEGlobS, 0, false>);
 }
 template <>
@@ -1049,6 +1088,7 @@ inline const void* PushTable<float>::get(int V, int dep, bool) {
     return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true>);
   }
   if (V == kSmemEGlobS) return reinterpret_cast<const void*>(&k_push<float, kSmemEGlobS, 0, true>);
+  if (V == kGlobESmemS) return reinterpret_cast<const void*>(&k_push<float, kGlobESmemS, 1, true>);
   return reinterpret_cast<const void*>(&k_push<float, kGlobEGlobS, 0, true>);
 }
 
@@ -1064,7 +1104,7 @@ struct Launchers {
   static size_t smem_bytes(int nx, int variant, int dep = 0) {
     const size_t eb = ((size_t)nx * sizeof(Real) + 15) & ~size_t(15);
     if (variant == kSmemESmemS) return (dep == 4 ? 3 : 2) * eb;
-    if (variant == kSmemEGlobS) return eb;
+    if (variant == kSmemEGlobS || variant == kGlobESmemS) return eb;
     return 0;
   }
 
@@ -1084,8 +1124,16 @@ struct Launchers {
     else if (dep == 4 && smem_bytes(d.nx, kSmemESmemS, 1) <= limit) {
       dep = 1;  // the two-word accumulator does not fit: one word
       variant = kSmemESmemS;
-    } else if (smem_bytes(d.nx, kSmemEGlobS) <= limit) variant = kSmemEGlobS;
-    if (variant != kSmemESmemS) dep = 0;
+    } else if (sizeof(Real) == 4 && smem_bytes(d.nx, kGlobESmemS) <= limit) {
+      // E does not fit beside the accumulator: gather it through L1 (read
+      // only).  FP32 only: FP64 shared-memory atomics are compare-and-swap
+      // loops and measured slower than FP64 global atomics (variant 1).
+      variant = kGlobESmemS;
+      if (dep == 4) dep = 1;
+    } else if (smem_bytes(d.nx, kSmemEGlobS) <= limit) {
+      variant = kSmemEGlobS;
+    }
+    if (variant == kGlobEGlobS) dep = 0;
     d.variant = variant;
     d.push_dep = dep;
     d.push_fast = fast;
@@ -1093,7 +1141,7 @@ struct Launchers {
     const void* fn = push_fn(d);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int block = 1024;
+    const int block = PushBlock<Real>::value;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
     if (e != cudaSuccess) return e;
@@ -1127,7 +1175,7 @@ struct Launchers {
                                      smem_bytes(d.nx, d.variant, d.push_dep), st);
     if (e != cudaSuccess) return e;
     if (after) cudaEventRecord(after, st);
-    if (d.variant == kSmemESmemS) {
+    if (d.variant == kSmemESmemS || d.variant == kGlobESmemS) {
       k_field<Real, true><<<d.grid_field, kFieldBlock, 0, st>>>(d);
     } else {
       k_field<Real, false><<<d.grid_field, kFieldBlock, 0, st>>>(d);
@@ -1157,7 +1205,7 @@ struct Launchers {
     if (smem_bytes(max_nx, kSmemESmemS, dp) > limit && dp == 4) dp = 1;
     const size_t sm = smem_bytes(max_nx, kSmemESmemS, dp);
     if (sm > limit) return cudaErrorInvalidValue;
-    const int minb = env_int("CASCADE_BATCH_MINB", 1) == 2 ? 2 : 1;
+    const int minb = env_int("CASCADE_BATCH_MINB", 2) == 1 ? 1 : 2;  // 2: measured faster
     const void* fn = batch_push_fn(dp, minb);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -1188,6 +1236,18 @@ struct Launchers {
     long long blocks = (count + 255) / 256;
     if (blocks > 8192) blocks = 8192;
     k_upload<Real><<<(int)blocks, 256, 0, st>>>(d, sp, first, count, off_src, u_src, bad);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t histogram(const Dev& d, int sp, int quantity, int nbins, double lo, double hi,
+                               unsigned long long* out, cudaStream_t st) {
+    const size_t sm = sizeof(unsigned int) * (size_t)nbins;
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_histogram<Real>),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(out, 0, sizeof(unsigned long long) * nbins, st);
+    if (e != cudaSuccess) return e;
+    k_histogram<Real><<<d.grid_push, 512, sm, st>>>(d, sp, quantity, nbins, lo, hi, out);
     return cudaGetLastError();
   }
 
@@ -1225,6 +1285,10 @@ struct Launchers {
     return Launchers<REAL>::batch_step(b, grid, block, smem, dep, s);                             \
   }                                                                                               \
   size_t partial_bytes_##SUFFIX() { return sizeof(REAL); }                                       \
+  cudaError_t histogram_##SUFFIX(const Dev& d, int sp, int q, int nb, double lo, double hi,          \
+                                 unsigned long long* out, cudaStream_t s) {                       \
+    return Launchers<REAL>::histogram(d, sp, q, nb, lo, hi, out, s);                              \
+  }                                                                                               \
   cudaError_t upload_##SUFFIX(const Dev& d, int sp, long long first, long long count, const double* o, \
                               const double* u, unsigned int* bad, cudaStream_t s) {               \
     return Launchers<REAL>::upload(d, sp, first, count, o, u, bad, s);                            \

@@ -294,3 +294,33 @@ def test_state_upload_rejects_particles_outside_the_grid():
     nan_u = {"elec": {"cell": [3], "off": [0.5], "u": [float("nan")]}, "posi": {"cell": [3], "off": [0.5], "u": [0.0]}}
     with pytest.raises(CascadeError):
         Cascade(dict(p, precision="fp32"), state=nan_u)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_phase_space_histogram(precision):
+    """On-device histograms equal numpy's histograms of the same particles
+    (integer work: exact in FP64), and match the oracle's momentum spectrum."""
+    p = dict(W.small_cascade(), precision=precision)
+    steps = 150
+    ref = oracle.Oracle(oracle_params(p))
+    ref.step(steps)
+    pr = ref.particles()
+    with Cascade(p) as c:
+        c.step(steps)
+        for s, q in ((0, -1), (1, 1)):
+            g = c.particles(s)
+            L = p["nx"] * p["dx"]
+            gam = np.sqrt(1.0 + g["u"] ** 2)
+            x = (g["cell"] + g["off"]) * p["dx"]
+            for quantity, vals, lo, hi in (("u", g["u"], -30.0, 30.0), ("gamma", gam, 1.0, 25.0), ("x", x, 0.0, L)):
+                h = c.histogram(s, quantity, 64, lo, hi)
+                want = np.histogram(vals, bins=64, range=(lo, hi))[0]
+                if precision == "fp64":
+                    assert np.array_equal(h, want), quantity
+                else:
+                    # values are FP32, binned in FP64 on both sides
+                    assert np.abs(h - want).sum() <= 2, quantity
+            sel = pr["q"] == q
+            h_ref = np.histogram(pr["u"][sel], bins=64, range=(-30.0, 30.0))[0]
+            h = c.histogram(s, "u", 64, -30.0, 30.0)
+            assert np.abs(h - h_ref).sum() <= (2 if precision == "fp64" else 0.02 * sel.sum())
