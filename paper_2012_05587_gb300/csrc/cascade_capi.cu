@@ -180,6 +180,7 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
   d.lpp_int = (int)floor(L);
   d.lpp_frac = L - (double)d.lpp_int;
   d.cap = params->particle_cap;
+  d.cap4 = pl.cap4;
   d.ph_cap = pl.ph_cap;
   d.dx = params->dx;
   d.dt = params->dt;

@@ -35,6 +35,7 @@ struct Dev {
   int n_pp;            // photon flight in steps
   int lpp_int;         // floor(l_pp / dx)
   long long cap;       // particle capacity per species
+  long long cap4;      // allocated particles per species (cap rounded up to 4)
   long long ph_cap;    // photon ring capacity (power of two)
   double dx, dt, dtdx, jscale, w;
   double gamma_thr, eps_gamma, lpp_frac, u_pair;
@@ -63,6 +64,7 @@ struct Dev {
   int push_dep;        // current accumulator, see AccOf in cascade_kernels.cuh
   int push_fast;       // 1: gamma from one reciprocal square root (FP32 only)
   int fine_deposit;    // FP32: two-word accumulator (CASCADE_FP32_MIXED_FINE)
+  int prefetch;        // particle kernel: iterations ahead to prefetch into L2 (0 = off)
   long long min_per_cta;  // particles per active CTA before another CTA is woken
   long long item_size;    // batched kernels: particles per work item (multiple of 4)
 };

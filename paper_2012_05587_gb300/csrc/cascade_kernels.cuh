@@ -53,6 +53,12 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 
 __device__ __forceinline__ void set_error(Ctl* ctl, int code) { atomicCAS(&ctl->err, 0, code); }
 
+// Bulk prefetch of [ptr, ptr + bytes) into L2 (a hint; bytes a multiple of 16,
+// ptr 16-byte aligned, the range inside an allocation).
+__device__ __forceinline__ void prefetch_l2(const void* ptr, unsigned bytes) {
+  if (bytes >= 16) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Seed: quiet start, pair j in cell j mod nx at offset (j div nx + 1/2)/ppc,
 // momenta u_spread * Box-Muller(Philox(counter = (j, 0), key = seed)).
@@ -553,7 +559,22 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   double gsum_total = 0.0;
+  const int pf = d.prefetch;  // iterations ahead that lane 0 prefetches its warp's particles
   for (long long it = 0; it < iters_cta; ++it) {
+    if (pf > 0 && lane == 0) {
+      const long long chp = first_wb + (it + pf) * stride + warp * 32;  // the warp's first chunk then
+      if (chp < C) {
+        const int sp = chp < C0 ? 0 : 1;
+        const long long bp = (chp - (sp ? C0 : 0)) * 4;
+        long long np = d.cap4 - bp;  // stay inside the allocation
+        if (np > 128) np = 128;
+        if (np > 0) {
+          prefetch_l2(d.cell[sp] + bp, (unsigned)(np * 4) & ~15u);
+          prefetch_l2(static_cast<const Real*>(d.off[sp]) + bp, (unsigned)(np * sizeof(Real)) & ~15u);
+          prefetch_l2(static_cast<const Real*>(d.u[sp]) + bp, (unsigned)(np * sizeof(Real)) & ~15u);
+        }
+      }
+    }
     const long long ch = first_wb + it * stride + warp * 32 + lane;
     int s = 0, cnt = 0;
     long long base = 0;
@@ -1148,6 +1169,8 @@ struct Launchers {
     if (per_sm < 1) per_sm = 1;
     d.block_push = block;
     d.grid_push = per_sm * num_sms;
+    d.prefetch = env_int("CASCADE_PUSH_PREFETCH", 1);  // one iteration ahead: measured +4.6%
+    if (d.prefetch < 0 || d.prefetch > 8) d.prefetch = 0;
     d.grid_field = (d.nx + 31) / 32;
     d.nxp = (d.nx + 31) & ~31;
     d.min_per_cta = d.nx > 2048 ? d.nx : 2048;
