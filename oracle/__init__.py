@@ -54,6 +54,8 @@ class OrcParams(ctypes.Structure):
         ("E0", ctypes.c_double), ("gamma_thr", ctypes.c_double),
         ("eps_gamma", ctypes.c_double), ("l_pp", ctypes.c_double),
         ("particle_cap", ctypes.c_int64),
+        ("j_m", ctypes.c_double), ("rho_gj", ctypes.c_double),
+        ("open_bc", ctypes.c_int32), ("pad_", ctypes.c_int32),
     ]
 
 
@@ -118,6 +120,8 @@ def _params(p: dict) -> OrcParams:
         n0=float(p["n0"]), u_spread=float(p["u_spread"]), seed=int(p["seed"]),
         E0=float(p["E0"]), gamma_thr=float(p["gamma_thr"]), eps_gamma=float(p["eps_gamma"]),
         l_pp=float(p["l_pp"]), particle_cap=int(p.get("particle_cap", 1 << 40)),
+        j_m=float(p.get("j_m", 0.0)), rho_gj=float(p.get("rho_gj", 0.0)),
+        open_bc=int(p.get("open_bc", 0)), pad_=0,
     )
 
 

@@ -29,6 +29,14 @@
  *   4. every lepton, in storage order: threshold emission with recoil;
  *   5. diagnostics at n+1.
  *
+ * Co-rotating frame (Section 7, Eq. 25-26): an optional background charge
+ * rho_GJ enters Gauss's law, dE/dx = rho - rho_GJ, and a background current
+ * j_m enters Ampere's law, dE/dt = -(J - j_m).  With open boundaries the
+ * field beyond the outermost edges equals the nearest edge, a particle that
+ * crosses x = 0 or x = L deposits the part of its path inside the domain and
+ * is removed at the end of the step, and a photon whose conversion point
+ * lies outside is not kept.
+ *
  * Representation: a particle sits at x = (cell + off) dx, cell integer,
  * off in [0, 1).  E and J live on edges: E[i] = E_{i+1/2}.  The charge of a
  * particle is shared between nodes cell and cell+1 with linear (CIC) weights.
@@ -57,6 +65,10 @@ typedef struct {
   double eps_gamma;    /* photon energy (m c^2) = f gamma_thr */
   double l_pp;         /* photon flight length before conversion */
   int64_t particle_cap;/* per species */
+  double j_m;          /* background current (co-rotating frame), 0 otherwise */
+  double rho_gj;       /* background charge density, 0 otherwise */
+  int32_t open_bc;     /* 0: periodic; 1: open boundaries */
+  int32_t pad_;
 } orc_params;
 
 typedef struct {
@@ -199,6 +211,7 @@ static int validate(const orc_params* p) {
   if (!(p->gamma_thr - p->eps_gamma >= 1.0)) return ORC_ERR_ARG;  /* recoil stays physical */
   if (!(p->eps_gamma / p->gamma_thr < 2.0 / 3.0)) return ORC_ERR_ARG; /* Eq. 1 delay > 0 */
   if (p->particle_cap < 1) return ORC_ERR_ARG;
+  if (p->open_bc != 0 && p->open_bc != 1) return ORC_ERR_ARG;
   return ORC_OK;
 }
 
@@ -308,17 +321,19 @@ static void convert_photons(orc_sim* s) {
 
 static void push_move_deposit(orc_sim* s) {
   const int32_t nx = s->p.nx;
+  const int open = s->p.open_bc;
   const double dt = s->p.dt, dtdx = s->dtdx;
   for (int32_t i = 0; i < nx; ++i) s->S[i] = 0.0;
   for (int64_t p = 0; p < s->np; ++p) {
     const double q = (double)s->q[p];
     int32_t c = s->cell[p];
     double o = s->off[p];
-    /* gather: linear interpolation between the two edges bracketing x */
+    /* gather: linear interpolation between the two edges bracketing x (open
+     * boundaries: beyond the outermost edges the field is that edge's) */
     int32_t ia, ib;
     double w;
-    if (o >= 0.5) { ia = c; ib = (c + 1 == nx) ? 0 : c + 1; w = o - 0.5; }
-    else          { ia = (c == 0) ? nx - 1 : c - 1; ib = c; w = o + 0.5; }
+    if (o >= 0.5) { ia = c; ib = (c + 1 == nx) ? (open ? nx - 1 : 0) : c + 1; w = o - 0.5; }
+    else          { ia = (c == 0) ? (open ? 0 : nx - 1) : c - 1; ib = c; w = o + 0.5; }
     double Ep = (1.0 - w) * s->E[ia] + w * s->E[ib];
     /* push: du/dt = q E */
     double u = s->u[p] + q * dt * Ep;
@@ -331,15 +346,23 @@ static void push_move_deposit(orc_sim* s) {
      * sub-segment between nodes; sum q * (offset change) per edge */
     if (o2 >= 1.0) {
       s->S[c] += q * (1.0 - o);
-      c2 = (c + 1 == nx) ? 0 : c + 1;
-      o2 = o2 - 1.0;
-      s->S[c2] += q * o2;
+      if (open && c + 1 == nx) {
+        c2 = -1;  /* left through x = L: the part inside is deposited */
+      } else {
+        c2 = (c + 1 == nx) ? 0 : c + 1;
+        o2 = o2 - 1.0;
+        s->S[c2] += q * o2;
+      }
     } else if (o2 < 0.0) {
       s->S[c] += q * (0.0 - o);
-      c2 = (c == 0) ? nx - 1 : c - 1;
-      o2 = o2 + 1.0;
-      s->S[c2] += q * (o2 - 1.0);
-      if (o2 >= 1.0) { o2 = 0.0; c2 = c; }  /* rounding landed on the node itself */
+      if (open && c == 0) {
+        c2 = -1;  /* left through x = 0 */
+      } else {
+        c2 = (c == 0) ? nx - 1 : c - 1;
+        o2 = o2 + 1.0;
+        s->S[c2] += q * (o2 - 1.0);
+        if (o2 >= 1.0) { o2 = 0.0; c2 = c; }  /* rounding landed on the node itself */
+      }
     } else {
       s->S[c] += q * (o2 - o);
     }
@@ -350,11 +373,28 @@ static void push_move_deposit(orc_sim* s) {
   }
 }
 
+/* Open boundaries: particles that left (cell -1) are removed, keeping the
+ * storage order of the rest. */
+static void remove_departed(orc_sim* s) {
+  int64_t k = 0;
+  for (int64_t p = 0; p < s->np; ++p) {
+    if (s->cell[p] < 0) {
+      s->n_species[s->q[p] > 0 ? 1 : 0]--;
+      continue;
+    }
+    s->cell[k] = s->cell[p]; s->off[k] = s->off[p]; s->u[k] = s->u[p];
+    s->gam[k] = s->gam[p]; s->q[k] = s->q[p];
+    k++;
+  }
+  s->np = k;
+}
+
+/* Ampere: dE/dt = -(J - j_m) (Eq. 26; j_m = 0 outside the co-rotating frame). */
 static void ampere(orc_sim* s) {
   const double dt = s->p.dt;
   for (int32_t i = 0; i < s->p.nx; ++i) {
     s->J[i] = s->jscale * s->S[i];
-    s->E[i] = s->E[i] - dt * s->J[i];
+    s->E[i] = s->E[i] - dt * (s->J[i] - s->p.j_m);
   }
 }
 
@@ -370,20 +410,22 @@ static void qed_emission(orc_sim* s) {
     s->u[p] = sgn * sqrt(g2 * g2 - 1.0);
     s->gam[p] = g2;
     if (k > 1) s->emit_multi++;
-    /* conversion point x + dir * l_pp, wrapped */
+    /* conversion point x + dir * l_pp, wrapped (open boundaries: a photon
+     * that would convert outside the domain is not kept) */
     int32_t cc;
     double oc;
+    int64_t ci;
     if (sgn > 0) {
       oc = s->off[p] + s->lpp_frac;
-      int64_t ci = (int64_t)s->cell[p] + s->lpp_int;
+      ci = (int64_t)s->cell[p] + s->lpp_int;
       if (oc >= 1.0) { oc = oc - 1.0; ci += 1; }
-      cc = wrap_cell(ci, s->p.nx);
     } else {
       oc = s->off[p] - s->lpp_frac;
-      int64_t ci = (int64_t)s->cell[p] - s->lpp_int;
+      ci = (int64_t)s->cell[p] - s->lpp_int;
       if (oc < 0.0) { oc = oc + 1.0; ci -= 1; if (oc >= 1.0) { oc = 0.0; ci += 1; } }
-      cc = wrap_cell(ci, s->p.nx);
     }
+    if (s->p.open_bc && (ci < 0 || ci >= s->p.nx)) continue;
+    cc = wrap_cell(ci, s->p.nx);
     if (grow_photons(s, s->nph + k)) { s->error = ORC_ERR_OOM; return; }
     for (int64_t m = 0; m < k; ++m) {
       s->ph_conv_step[s->nph] = conv;
@@ -400,10 +442,10 @@ static void charge_density(orc_sim* s) {
   for (int32_t i = 0; i < nx; ++i) s->rho_dx[i] = 0.0;
   for (int64_t p = 0; p < s->np; ++p) {
     int32_t c = s->cell[p];
-    int32_t c1 = (c + 1 == nx) ? 0 : c + 1;
     double qw = (double)s->q[p] * s->w;
     s->rho_dx[c] += qw * (1.0 - s->off[p]);
-    s->rho_dx[c1] += qw * s->off[p];
+    if (c + 1 < nx) s->rho_dx[c + 1] += qw * s->off[p];
+    else if (!s->p.open_bc) s->rho_dx[0] += qw * s->off[p];  /* periodic node nx = node 0 */
   }
 }
 
@@ -418,11 +460,12 @@ static void diagnostics(orc_sim* s, orc_diag* d) {
     ue += 0.5 * s->E[i] * s->E[i] * s->p.dx;
   }
   for (int64_t p = 0; p < s->np; ++p) uk += s->w * s->gam[p];
-  /* Gauss on node i between edges i-1/2 and i+1/2: E[i] - E[i-1] = dx rho_i */
+  /* Gauss on node i between edges i-1/2 and i+1/2: E[i] - E[i-1] =
+   * dx (rho_i - rho_GJ); with open boundaries only the interior nodes */
   charge_density(s);
-  for (int32_t i = 0; i < nx; ++i) {
+  for (int32_t i = s->p.open_bc ? 1 : 0; i < nx; ++i) {
     int32_t im = (i == 0) ? nx - 1 : i - 1;
-    double r = fabs(s->E[i] - s->E[im] - s->rho_dx[i]);
+    double r = fabs(s->E[i] - s->E[im] - (s->rho_dx[i] - s->p.rho_gj * s->p.dx));
     if (r > gres) gres = r;
   }
   d->step = s->step;
@@ -447,6 +490,7 @@ int orc_step(orc_sim* s, int32_t nsteps, orc_diag* out) {
     convert_photons(s);
     if (s->error) return s->error;
     push_move_deposit(s);
+    if (s->p.open_bc) remove_departed(s);
     ampere(s);
     qed_emission(s);
     if (s->error) return s->error;

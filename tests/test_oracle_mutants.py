@@ -11,6 +11,7 @@ import os
 import pytest
 
 import oracle
+import test_oracle_corotating as corot
 import test_oracle_pins as pins
 
 ALL_PINS = [
@@ -30,6 +31,12 @@ ALL_PINS = [
     pins.test_threshold_tie_emits,
     pins.test_in_place_conversion,
     lambda lib=None: pins.test_frozen_field_growth_rate(0.1, lib),
+    corot.test_background_current_drives_the_uniform_mode,
+    corot.test_corotating_equilibrium_is_stationary,
+    corot.test_open_boundary_removes_departing_particles,
+    corot.test_open_boundary_outflow_keeps_gauss,
+    corot.test_open_boundary_gather_uses_the_edge_field,
+    corot.test_open_boundary_drops_photons_converting_outside,
 ]
 
 # (name, original text, mutated text)
@@ -47,7 +54,7 @@ MUTANTS = [
     ("deposit_sign", "s->S[c] += q * (o2 - o);", "s->S[c] += q * (o - o2);"),
     ("deposit_crossing_edge", "s->S[c2] += q * o2;", "s->S[c] += q * o2;"),
     ("deposit_backward_term", "s->S[c2] += q * (o2 - 1.0);", "s->S[c2] += q * (1.0 - o2);"),
-    ("ampere_sign", "s->E[i] = s->E[i] - dt * s->J[i];", "s->E[i] = s->E[i] + dt * s->J[i];"),
+    ("ampere_sign", "s->E[i] = s->E[i] - dt * (s->J[i] - s->p.j_m);", "s->E[i] = s->E[i] + dt * (s->J[i] - s->p.j_m);"),
     ("current_scale", "s->jscale = p->n0 * p->dx / ((double)p->ppc * p->dt);",
      "s->jscale = 2.0 * p->n0 * p->dx / ((double)p->ppc * p->dt);"),
     ("recoil_dropped", "double g2 = g - (double)k * eps;", "double g2 = g;"),
@@ -59,6 +66,12 @@ MUTANTS = [
     ("photon_direction_lost", "s->ph_dir[s->nph] = (int8_t)(sgn > 0 ? 1 : -1);", "s->ph_dir[s->nph] = 1;"),
     ("kinetic_energy_weight", "uk += s->w * s->gam[p];", "uk += s->gam[p];"),
     ("field_energy_half", "ue += 0.5 * s->E[i] * s->E[i] * s->p.dx;", "ue += s->E[i] * s->E[i] * s->p.dx;"),
+    ("background_current_sign", "s->E[i] = s->E[i] - dt * (s->J[i] - s->p.j_m);",
+     "s->E[i] = s->E[i] - dt * (s->J[i] + s->p.j_m);"),
+    ("background_charge_sign", "(s->rho_dx[i] - s->p.rho_gj * s->p.dx)", "(s->rho_dx[i] + s->p.rho_gj * s->p.dx)"),
+    ("open_gather_wraps", "ia = (c == 0) ? (open ? 0 : nx - 1) : c - 1;", "ia = (c == 0) ? nx - 1 : c - 1;"),
+    ("departing_deposit", "s->S[c] += q * (1.0 - o);", "s->S[c] += q * (0.5 - o);"),
+    ("photon_outside_kept", "if (s->p.open_bc && (ci < 0 || ci >= s->p.nx)) continue;", "if (0) continue;"),
 ]
 
 
