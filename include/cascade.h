@@ -81,6 +81,14 @@ typedef struct {
   int64_t photon_cap;    /* photons in flight; 0 = particle_cap rounded up to a power of 2 */
   int32_t precision;     /* cascade_precision */
   int32_t diag_ring;     /* per-step records kept on the device; 0 = 4096 */
+  /* Co-rotating frame (Section 7, Eq. 25-26); all zero for the Section 3 model. */
+  double j_m;            /* background current: dE/dt = -(J - j_m) */
+  double rho_gj;         /* background charge: dE/dx = rho - rho_GJ (Gauss diagnostic) */
+  int32_t open_bc;       /* 1: open boundaries -- the field beyond the outermost edges
+                            equals the nearest edge, particles crossing x = 0 or x = L
+                            deposit the path inside and are removed, photons that would
+                            convert outside are not kept; 0: periodic */
+  int32_t reserved_;     /* set to 0 */
 } cascade_params;
 
 /* One record per step, taken after the step (time t = step dt).  Energies are

@@ -41,6 +41,8 @@ class cascade_params(ctypes.Structure):
         ("eps_gamma", ctypes.c_double), ("l_pp", ctypes.c_double),
         ("particle_cap", ctypes.c_int64), ("photon_cap", ctypes.c_int64),
         ("precision", ctypes.c_int32), ("diag_ring", ctypes.c_int32),
+        ("j_m", ctypes.c_double), ("rho_gj", ctypes.c_double),
+        ("open_bc", ctypes.c_int32), ("reserved_", ctypes.c_int32),
     ]
 
 
@@ -151,6 +153,8 @@ def make_params(p: dict) -> cascade_params:
         l_pp=float(p["l_pp"]), particle_cap=int(p.get("particle_cap", 1 << 20)),
         photon_cap=int(p.get("photon_cap", 0)), precision=int(prec),
         diag_ring=int(p.get("diag_ring", 0)),
+        j_m=float(p.get("j_m", 0.0)), rho_gj=float(p.get("rho_gj", 0.0)),
+        open_bc=int(p.get("open_bc", 0)), reserved_=0,
     )
 
 

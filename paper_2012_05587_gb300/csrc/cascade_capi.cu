@@ -62,6 +62,8 @@ int validate(const cascade_params* p) {
            p->precision != CASCADE_FP32_MIXED_FINE)
     why = "unknown precision";
   else if (p->diag_ring < 0) why = "diag_ring < 0";
+  else if (p->open_bc != 0 && p->open_bc != 1) why = "open_bc must be 0 or 1";
+  else if (!isfinite(p->j_m) || !isfinite(p->rho_gj)) why = "j_m and rho_gj must be finite";
   if (why) {
     snprintf(g_msg, sizeof(g_msg), "invalid parameters: %s", why);
     return CASCADE_ERR_INVALID_ARG;
@@ -193,7 +195,15 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
   d.u_pair = sqrt(hh * hh - 1.0);
   d.ring_n = pl.ring;
   d.fine_deposit = params->precision == CASCADE_FP32_MIXED_FINE ? 1 : 0;
+  d.open_bc = params->open_bc;
+  d.j_m = params->j_m;
+  d.rho_gj = params->rho_gj;
   e = params->precision == CASCADE_FP64 ? configure_fp64(d, h->num_sms) : configure_fp32(d, h->num_sms);
+  if (e == cudaErrorInvalidValue && params->open_bc) {
+    snprintf(g_msg, sizeof(g_msg), "open boundaries need the grid's E or current to fit shared memory (nx = %d)",
+             params->nx);
+    return CASCADE_ERR_INVALID_ARG;
+  }
   if (e != cudaSuccess) return cuda_fail(e, "configure");
 
   // device memory
@@ -226,6 +236,16 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
     long long it = (mult > 0 ? mult : 64) * (long long)d.nx;
     if (it < 16384) it = 16384;
     d.item_size = (it + 3) & ~3LL;
+  }
+  if (d.open_bc) {
+    // departures per step are bounded by the particles next to the boundaries
+    d.hole_cap = (pl.cap4 / 16 > 65536) ? pl.cap4 / 16 : 65536;
+    for (int sp = 0; sp < 2; ++sp) {
+      d.holes[sp] = static_cast<long long*>(h->dalloc(sizeof(long long) * d.hole_cap));
+      d.hole_a[sp] = static_cast<long long*>(h->dalloc(sizeof(long long) * d.hole_cap));
+      d.hole_b[sp] = static_cast<long long*>(h->dalloc(sizeof(long long) * d.hole_cap));
+      if (!d.holes[sp] || !d.hole_a[sp] || !d.hole_b[sp]) return CASCADE_ERR_OOM;
+    }
   }
   d.uk_part = static_cast<double*>(h->dalloc(sizeof(double) * d.grid_push));
   d.diag_part = static_cast<double*>(h->dalloc(sizeof(double) * 4 * d.grid_field));
@@ -803,6 +823,10 @@ int cascade_batch_admit(cascade_batch_t* b, const cascade_params* params, int32_
   if (!same_kernel_class(params->precision, b->precision)) {
     snprintf(g_msg, sizeof(g_msg), "member precision %d differs from the batch's %d", params->precision,
              b->precision);
+    return CASCADE_ERR_INVALID_ARG;
+  }
+  if (params->open_bc) {
+    snprintf(g_msg, sizeof(g_msg), "batch members are periodic (open_bc = 0)");
     return CASCADE_ERR_INVALID_ARG;
   }
   if (params->nx > b->max_nx) {

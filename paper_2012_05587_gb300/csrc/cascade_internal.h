@@ -25,6 +25,11 @@ struct Ctl {
   int active_blocks;              // particle-kernel CTAs that work in the current step
   unsigned int field_ticket;      // last-block detection in the field kernel
   int pad_;
+  // open boundaries: departed particles of the current step and the
+  // compaction that fills their slots
+  unsigned long long n_holes[2];  // departed (hole-list entries, may exceed the list)
+  unsigned long long na[2];       // holes below the new count
+  unsigned long long nb[2];       // live particles at or above the new count
 };
 
 // Everything a kernel needs about one cascade, passed by value.
@@ -65,6 +70,13 @@ struct Dev {
   int push_fast;       // 1: gamma from one reciprocal square root (FP32 only)
   int fine_deposit;    // FP32: two-word accumulator (CASCADE_FP32_MIXED_FINE)
   int prefetch;        // particle kernel: iterations ahead to prefetch into L2 (0 = off)
+  int open_bc;         // 1: open boundaries (co-rotating frame runs), 0: periodic
+  double j_m;          // background current in Ampere's law
+  double rho_gj;       // background charge in Gauss's law (diagnostic)
+  long long hole_cap;  // open boundaries: entries per species of each list below
+  long long* holes[2]; // departed particle indices
+  long long* hole_a[2];// holes below the new count
+  long long* hole_b[2];// live particles at or above the new count
   long long min_per_cta;  // particles per active CTA before another CTA is woken
   long long item_size;    // batched kernels: particles per work item (multiple of 4)
 };

@@ -260,7 +260,11 @@ __device__ __forceinline__ void set_scales(PushState<Real, DEP>& st, double pcou
 // Advance four consecutive particles of species s starting at index base
 // (cnt of them valid; the whole warp calls this together).  Returns the sum
 // of their gamma after the step.
-template <class Real, int V, int DEP, bool FAST>
+// OPEN: open boundaries (Section 7 runs): the gather clamps to the outermost
+// edges, a particle crossing x = 0 or x = L deposits the part of its path
+// inside and is marked departed (cell -1, index appended to the hole list),
+// a photon whose conversion point lies outside is not kept.
+template <class Real, int V, int DEP, bool FAST, bool OPEN>
 __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP>& st, int s, long long base,
                                          int cnt, int lane) {
   typedef typename AccOf<Real, DEP>::type Acc;
@@ -289,6 +293,17 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
   }
   const Real q = s ? one : -one;
   const Real qdt = s ? dt : -dt;
+  // live[j]: particle j exists and has not departed (a departed particle is
+  // only still stored if the hole list overflowed; it stays inert)
+  bool live[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    live[j] = j < cnt;
+    if (OPEN && cl[j] < 0) {
+      live[j] = false;
+      cl[j] = 0;
+    }
+  }
 
   // gather: linear between the two edges bracketing each particle
   Real Ep[4];
@@ -297,8 +312,8 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
     const int c = cl[j];
     const Real o = of[j];
     const bool hi = o >= half;
-    const int ia = hi ? c : ((c == 0) ? nx - 1 : c - 1);
-    const int ib = hi ? ((c + 1 == nx) ? 0 : c + 1) : c;
+    const int ia = hi ? c : ((c == 0) ? (OPEN ? 0 : nx - 1) : c - 1);
+    const int ib = hi ? ((c + 1 == nx) ? (OPEN ? nx - 1 : 0) : c + 1) : c;
     const Real w = hi ? o - half : o + half;
     Real Ea, Eb;
     if (V == kGlobEGlobS || V == kGlobESmemS) {
@@ -315,6 +330,7 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
   // charge-conserving current: q * (offset change) per edge crossed
   Real g[4], a1[4], a2[4];
   int e1[4], e2[4];
+  bool departed[4] = {false, false, false, false};
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = cl[j];
@@ -326,31 +342,45 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
     int c2 = c;
     Real b1, b2 = zero;
     int f2 = -1;
+    bool gone = false;
     if (o2 >= one) {
       b1 = q * (one - o);
-      c2 = (c + 1 == nx) ? 0 : c + 1;
-      o2 = o2 - one;
-      f2 = c2;
-      b2 = q * o2;
+      if (OPEN && c + 1 == nx) {
+        gone = true;  // left through x = L: the part inside is deposited
+      } else {
+        c2 = (c + 1 == nx) ? 0 : c + 1;
+        o2 = o2 - one;
+        f2 = c2;
+        b2 = q * o2;
+      }
     } else if (o2 < zero) {
       b1 = q * (zero - o);
-      c2 = (c == 0) ? nx - 1 : c - 1;
-      o2 = o2 + one;
-      f2 = c2;
-      b2 = q * (o2 - one);
-      if (o2 >= one) {
-        o2 = zero;
-        c2 = c;
+      if (OPEN && c == 0) {
+        gone = true;  // left through x = 0
+      } else {
+        c2 = (c == 0) ? nx - 1 : c - 1;
+        o2 = o2 + one;
+        f2 = c2;
+        b2 = q * (o2 - one);
+        if (o2 >= one) {
+          o2 = zero;
+          c2 = c;
+        }
       }
     } else {
       b1 = q * (o2 - o);
     }
-    const bool valid = j < cnt;
+    const bool valid = live[j];
     e1[j] = valid ? c : -1;
     e2[j] = valid ? f2 : -1;
     a1[j] = b1;
     a2[j] = b2;
-    g[j] = valid ? gj : one;
+    if (OPEN && valid && gone) {
+      departed[j] = true;
+      live[j] = false;
+      c2 = -1;
+    }
+    g[j] = live[j] ? gj : one;
     cl[j] = c2;
     of[j] = o2;
     uu[j] = u;
@@ -390,6 +420,33 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
 
   // QED (Section 2): threshold emission with recoil; photons appended with
   // one warp-wide scan and one global atomic per slot that has emitters
+  if (OPEN) {
+    // departed particles: their indices join the species' hole list (one
+    // warp-wide scan and one atomic per warp)
+    const int nd = (int)departed[0] + (int)departed[1] + (int)departed[2] + (int)departed[3];
+    if (__any_sync(kFull, nd > 0)) {
+      int incl = nd;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int tot = __shfl_sync(kFull, incl, 31);
+      unsigned long long b0 = 0;
+      if (lane == 0) b0 = atomicAdd(&st.ctl->n_holes[s], (unsigned long long)tot);
+      b0 = __shfl_sync(kFull, b0, 0);
+      unsigned long long pos = b0 + incl - nd;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (departed[j]) {
+          if ((long long)pos < d.hole_cap) d.holes[s][pos] = base + j;
+          else set_error(st.ctl, CASCADE_ERR_CAPACITY);
+          ++pos;
+        }
+      }
+    }
+  }
+
   const bool hot = (g[0] >= thr) | (g[1] >= thr) | (g[2] >= thr) | (g[3] >= thr) |
                    !(g[0] <= Real(1e30)) | !(g[1] <= Real(1e30)) | !(g[2] <= Real(1e30)) |
                    !(g[3] <= Real(1e30));
@@ -457,6 +514,7 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
         if (k > 1) atomicAdd(reinterpret_cast<unsigned long long*>(&st.ctl->emit_multi), 1ull);
         uu[j] = u;
         g[j] = gj;
+        if (OPEN && (ci < 0 || ci >= nx)) k = 0;  // converts outside the domain: not kept
       }
       const unsigned em = __ballot_sync(kFull, k > 0);
       if (em) {
@@ -486,6 +544,11 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
     }
   }
 
+  if (OPEN) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (!live[j]) cl[j] = -1;  // departed now or before
+  }
   if (cnt == 4) {
     st4(cellp, cl);
     st4(offp, of);
@@ -502,7 +565,7 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
   }
   Real gs = zero;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) gs += (j < cnt) ? g[j] : zero;
+  for (int j = 0; j < 4; ++j) gs += live[j] ? g[j] : zero;
   return gs;
 }
 
@@ -518,7 +581,7 @@ struct PushBlock {
   static constexpr int value = sizeof(Real) == 8 ? 512 : 1024;
 };
 
-template <class Real, int V, int DEP, bool FAST>
+template <class Real, int V, int DEP, bool FAST, bool OPEN>
 __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
   typedef typename AccOf<Real, DEP>::type Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -584,7 +647,7 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
       const long long N = s ? N1 : N0;
       cnt = (int)min(4LL, N - base);
     }
-    gsum_total += (double)process4<Real, V, DEP, FAST>(d, st, s, base, cnt, lane);
+    gsum_total += (double)process4<Real, V, DEP, FAST, OPEN>(d, st, s, base, cnt, lane);
   }
 
   // sum of gamma over the CTA (FP64)
@@ -654,6 +717,16 @@ __device__ __forceinline__ void finish_step(const Dev& d, const double r[4], dou
   const long long cc = ctl->conv_count;
   ctl->n[0] += cc;
   ctl->n[1] += cc;
+  if (d.open_bc) {
+    // departed particles are gone (compaction filled their slots)
+    for (int sp = 0; sp < 2; ++sp) {
+      const long long h = (long long)ctl->n_holes[sp];
+      ctl->n[sp] -= h < d.hole_cap ? h : d.hole_cap;
+      ctl->n_holes[sp] = 0ull;
+      ctl->na[sp] = 0ull;
+      ctl->nb[sp] = 0ull;
+    }
+  }
   ctl->pairs_total += cc;
   ctl->ph_head = ctl->conv_end;
   unsigned long long em = ctl->emit_count;
@@ -717,7 +790,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(Dev d) {
       d.S_glob[i] = 0.0;
     }
     const double J = d.jscale * S;
-    const double E = d.E[i] - d.dt * J;
+    const double E = d.E[i] - d.dt * (J - d.j_m);  // Eq. 26 (j_m = 0 outside the co-rotating frame)
     d.E[i] = E;
     d.J[i] = J;
     v[0] = E;
@@ -754,6 +827,49 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(Dev d) {
   if (threadIdx.x == 0) {
     ctl->field_ticket = 0u;
     finish_step(d, r, gs[0]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Open boundaries: fill the slots of departed particles.  With N particles
+// processed and H departed, the new count is N - H; live particles at or
+// above it move into the holes below it (there are as many of each), so the
+// cost is O(H), not O(N).
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void k_compact_plan(Dev d) {
+  Ctl* ctl = d.ctl;
+  const long long cc = ctl->conv_count;
+  for (int s = 0; s < 2; ++s) {
+    const long long N = ctl->n[s] + cc;
+    long long H = (long long)ctl->n_holes[s];
+    H = H < d.hole_cap ? H : d.hole_cap;
+    const long long N2 = N - H;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < H;
+         t += (long long)gridDim.x * blockDim.x) {
+      if (d.cell[s][N2 + t] >= 0) d.hole_b[s][atomicAdd(&ctl->nb[s], 1ull)] = N2 + t;
+      const long long h = d.holes[s][t];
+      if (h < N2) d.hole_a[s][atomicAdd(&ctl->na[s], 1ull)] = h;
+    }
+  }
+}
+
+template <class Real>
+__global__ void k_compact_move(Dev d) {
+  Ctl* ctl = d.ctl;
+  for (int s = 0; s < 2; ++s) {
+    const long long na = (long long)ctl->na[s];
+    const long long nb = (long long)ctl->nb[s];
+    const long long n = na < nb ? na : nb;  // equal unless the hole list overflowed
+    Real* off = static_cast<Real*>(d.off[s]);
+    Real* u = static_cast<Real*>(d.u[s]);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+      const long long to = d.hole_a[s][k], from = d.hole_b[s][k];
+      d.cell[s][to] = d.cell[s][from];
+      off[to] = off[from];
+      u[to] = u[from];
+    }
   }
 }
 
@@ -939,7 +1055,7 @@ __global__ void __launch_bounds__(512, MINB) k_batch_push(BatchDev b) {
         base = ch * 4;
         cnt = (int)min(4LL, p1 - base);
       }
-      gsum += (double)process4<Real, kSmemESmemS, DEP, true>(d, st, s, base, cnt, lane);
+      gsum += (double)process4<Real, kSmemESmemS, DEP, true, false>(d, st, s, base, cnt, lane);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gsum += __shfl_down_sync(kFull, gsum, o);
@@ -972,7 +1088,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_batch_field(BatchDev b) {
     const double S = d.S_glob[i];
     d.S_glob[i] = 0.0;
     const double J = d.jscale * S;
-    const double E = d.E[i] - d.dt * J;
+    const double E = d.E[i] - d.dt * (J - d.j_m);
     d.E[i] = E;
     d.J[i] = J;
     v[0] += E;
@@ -1034,6 +1150,7 @@ __global__ void k_histogram(Dev d, int s, int quantity, int nbins, double lo, do
   const Real* u = static_cast<const Real*>(d.u[s]);
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
+    if (d.cell[s][p] < 0) continue;  // departed (open boundaries)
     double v;
     if (quantity == 0) v = (double)u[p];
     else if (quantity == 1) v = sqrt(1.0 + (double)u[p] * (double)u[p]);
@@ -1061,11 +1178,12 @@ __global__ void k_gauss_deposit(Dev d, double* rho_dx) {
     const int s = t < N0 ? 0 : 1;
     const long long p = s ? t - N0 : t;
     const int c = d.cell[s][p];
+    if (c < 0) continue;  // departed (open boundaries)
     const double o = (double)static_cast<const Real*>(d.off[s])[p];
-    const int c1 = (c + 1 == d.nx) ? 0 : c + 1;
     const double qw = (s ? 1.0 : -1.0) * d.w;
     atomicAdd(&rho_dx[c], qw * (1.0 - o));
-    atomicAdd(&rho_dx[c1], qw * o);
+    if (c + 1 < d.nx) atomicAdd(&rho_dx[c + 1], qw * o);
+    else if (!d.open_bc) atomicAdd(&rho_dx[0], qw * o);  // periodic: node nx is node 0
   }
 }
 
@@ -1073,9 +1191,10 @@ template <class Real>
 __global__ void k_gauss_reduce(Dev d, const double* rho_dx, double* out) {
   __shared__ double sh[128];
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int i = threadIdx.x; i < d.nx; i += blockDim.x) {
+  // dE/dx = rho - rho_GJ (Eq. 25); with open boundaries interior nodes only
+  for (int i = threadIdx.x + (d.open_bc ? 1 : 0); i < d.nx; i += blockDim.x) {
     const int im = (i == 0) ? d.nx - 1 : i - 1;
-    v[2] = fmax(v[2], fabs(d.E[i] - d.E[im] - rho_dx[i]));
+    v[2] = fmax(v[2], fabs(d.E[i] - d.E[im] - (rho_dx[i] - d.rho_gj * d.dx)));
   }
   block_reduce4(v, sh);
   if (threadIdx.x == 0) {
@@ -1093,24 +1212,32 @@ __global__ void k_gauss_reduce(Dev d, const double* rho_dx, double* out) {
 // accumulator.
 template <class Real>
 struct PushTable {
-  static const void* get(int V, int dep, bool fast);
+  static const void* get(int V, int dep, bool fast, bool open);
 };
 template <>
-inline const void* PushTable<double>::get(int V, int, bool) {
-  if (V == kSmemESmemS) return reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false>);
-  if (V == kSmemEGlobS) return reinterpret_cast<const void*>(&k_push<double, kSmemEGlobS, 0, false>);
-  if (V == kGlobESmemS) return reinterpret_cast<const void*>(&k_push<double, kGlobESmemS, 0, false>);
-  return reinterpret_cast<const void*>(&k_push<double, kGlobEGlobS, 0, false>);
+inline const void* PushTable<double>::get(int V, int, bool, bool open) {
+  if (V == kSmemESmemS)
+    return open ? reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false, true>)
+                : reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false, false>);
+  if (V == kSmemEGlobS)
+    return open ? reinterpret_cast<const void*>(&k_push<double, kSmemEGlobS, 0, false, true>)
+                : reinterpret_cast<const void*>(&k_push<double, kSmemEGlobS, 0, false, false>);
+  if (V == kGlobESmemS) return reinterpret_cast<const void*>(&k_push<double, kGlobESmemS, 0, false, false>);
+  return reinterpret_cast<const void*>(&k_push<double, kGlobEGlobS, 0, false, false>);
 }
 template <>
-inline const void* PushTable<float>::get(int V, int dep, bool) {
+inline const void* PushTable<float>::get(int V, int dep, bool, bool open) {
   if (V == kSmemESmemS) {
-    if (dep == 4) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 4, true>);
-    return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true>);
+    if (open) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, true>);
+    if (dep == 4) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 4, true, false>);
+    return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, false>);
   }
-  if (V == kSmemEGlobS) return reinterpret_cast<const void*>(&k_push<float, kSmemEGlobS, 0, true>);
-  if (V == kGlobESmemS) return reinterpret_cast<const void*>(&k_push<float, kGlobESmemS, 1, true>);
-  return reinterpret_cast<const void*>(&k_push<float, kGlobEGlobS, 0, true>);
+  if (V == kSmemEGlobS) return reinterpret_cast<const void*>(&k_push<float, kSmemEGlobS, 0, true, false>);
+  if (V == kGlobESmemS) {
+    if (open) return reinterpret_cast<const void*>(&k_push<float, kGlobESmemS, 1, true, true>);
+    return reinterpret_cast<const void*>(&k_push<float, kGlobESmemS, 1, true, false>);
+  }
+  return reinterpret_cast<const void*>(&k_push<float, kGlobEGlobS, 0, true, false>);
 }
 
 inline int env_int(const char* name, int dflt) {
@@ -1129,7 +1256,9 @@ struct Launchers {
     return 0;
   }
 
-  static const void* push_fn(const Dev& d) { return PushTable<Real>::get(d.variant, d.push_dep, d.push_fast != 0); }
+  static const void* push_fn(const Dev& d) {
+    return PushTable<Real>::get(d.variant, d.push_dep, d.push_fast != 0, d.open_bc != 0);
+  }
 
   static cudaError_t configure(Dev& d, int num_sms) {
     const size_t limit = 200 * 1024;
@@ -1155,6 +1284,13 @@ struct Launchers {
       variant = kSmemEGlobS;
     }
     if (variant == kGlobEGlobS) dep = 0;
+    if (d.open_bc) {
+      // open boundaries are built for the shared-memory accumulator variants
+      // (plus E in shared memory with global FP64 atomics in FP64)
+      if (dep == 4) dep = 1;
+      if (variant == kGlobEGlobS || (sizeof(Real) == 8 && variant == kGlobESmemS))
+        return cudaErrorInvalidValue;
+    }
     d.variant = variant;
     d.push_dep = dep;
     d.push_fast = fast;
@@ -1198,6 +1334,10 @@ struct Launchers {
                                      smem_bytes(d.nx, d.variant, d.push_dep), st);
     if (e != cudaSuccess) return e;
     if (after) cudaEventRecord(after, st);
+    if (d.open_bc) {
+      k_compact_plan<Real><<<64, 256, 0, st>>>(d);
+      k_compact_move<Real><<<64, 256, 0, st>>>(d);
+    }
     if (d.variant == kSmemESmemS || d.variant == kGlobESmemS) {
       k_field<Real, true><<<d.grid_field, kFieldBlock, 0, st>>>(d);
     } else {

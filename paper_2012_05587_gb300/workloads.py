@@ -102,3 +102,36 @@ def serving_requests(n: int = 2000, rate: float = 50.0, run: int = 0, precision:
         q["arrival"] = t
         out.append(q)
     return out
+
+
+def corotating(nx: int = 10000, precision: str = "fp32", gamma_thr: float = 5000.0, eps_gamma: float = 50.0,
+               dt: float = 1e-3, dx: float = 0.1, ppc: int = 4, l_pp: float = 0.0) -> dict:
+    """Co-rotating-frame run of Section 7, in units of n_GJ = |rho_GJ| / e and
+    omega_p,GJ: L = nx dx (1000 in the paper), dx = 0.1, dt = 1e-3, open
+    boundaries, rho_GJ = -1, j_m = -1.5 rho_GJ c = 1.5, gamma_thr = 5000,
+    f = 0.01.  ppc is the positron count per cell (electrons: 2 ppc), so the
+    weight n0 dx / ppc with n0 = 1 gives densities 2 and 1."""
+    return dict(nx=nx, ppc=ppc, dx=dx, dt=dt, n0=1.0, u_spread=0.0, seed=seed_of(6), E0=0.0,
+                gamma_thr=gamma_thr, eps_gamma=eps_gamma, l_pp=l_pp, j_m=1.5, rho_gj=-1.0, open_bc=1,
+                precision=precision, particle_cap=max(1 << 20, 64 * nx * ppc), diag_ring=1 << 16)
+
+
+def corotating_state(p: dict):
+    """Cold initial state of Section 7: electrons of density 2 and positrons
+    of density 1, evenly spaced (rho = rho_GJ = -1, so E = 0 satisfies
+    Gauss's law), drifting with v = -1/2 and +1/2 so that the current equals
+    j_m = 1.5.  Returns ((cell, offset, u, q) arrays, E)."""
+    nx, ppc = p["nx"], p["ppc"]
+    v = 0.5
+    u = v / math.sqrt(1.0 - v * v)
+    cells, offs, us, qs = [], [], [], []
+    for n, uu, q in ((2 * ppc, -u, -1), (ppc, u, 1)):
+        i = np.repeat(np.arange(nx), n)
+        k = np.tile(np.arange(n), nx)
+        cells.append(i)
+        offs.append((k + 0.5) / n)
+        us.append(np.full(len(i), uu))
+        qs.append(np.full(len(i), q))
+    state = (np.concatenate(cells).astype(np.int32), np.concatenate(offs), np.concatenate(us),
+             np.concatenate(qs).astype(np.int8))
+    return state, np.zeros(nx)

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_the_header_layout():
     # cascade_params: 2 int32, 9 double, 1 uint64 ... laid out without padding surprises
-    assert ctypes.sizeof(capi.cascade_params) == 4 * 2 + 8 * 9 + 8 * 2 + 4 * 2
+    assert ctypes.sizeof(capi.cascade_params) == 4 * 2 + 8 * 9 + 8 * 2 + 4 * 2 + 8 * 2 + 4 * 2
     assert ctypes.sizeof(capi.cascade_diag_t) == 8 * 14
 
 
