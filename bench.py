@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cap", type=int, default=0, help="particle cap per species (0 = the workload's)")
     ap.add_argument("--ppc", type=int, default=0, help="seed particles per cell per species (0 = the workload's)")
-    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "sweep", "paper"],
+    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "sweep", "paper", "corotating"],
                     help="large: one large cascade (default); batch: the 256-cascade parameter scan in one "
                          "launch per step; serve: Poisson arrivals admitted by footprint; sweep: FP32 vs FP64 "
                          "errors of the ensemble diagnostics")
@@ -67,7 +67,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--fp64-sample", type=int, default=8, help="cascades run one at a time in FP64 for comparison")
     ap.add_argument("--paper-time", type=float, default=12.0, help="paper workload: simulated time (1/omega_p)")
-    ap.add_argument("--save-series", default="", help="paper workload: directory for the per-step series")
+    ap.add_argument("--save-series", default="", help="paper/corotating workloads: directory for the series")
+    ap.add_argument("--corot-time", type=float, default=200.0, help="corotating workload: simulated time")
     return ap.parse_args()
 
 

@@ -295,5 +295,51 @@ def run_paper(args) -> int:
     return 0
 
 
+def run_corotating(args) -> int:
+    """Section 7 at the paper's parameters (L = 1000, dx = 0.1, dt = 1e-3,
+    gamma_thr = 5000, f = 0.01, open boundaries, j_m = -1.5 rho_GJ): time to
+    the first pairs, pair count, peak gap field, particle-steps/s; optionally
+    a space-time map of E every 100 steps (the quantity of Fig. 4a)."""
+    import torch
+
+    from paper_2012_05587_gb300 import Cascade, workloads as W
+
+    p = W.corotating(precision=args.precision)
+    state, E = W.corotating_state(p)
+    c, o, u, q = state
+    e, ps_ = q < 0, q > 0
+    st = {"elec": {"cell": c[e], "off": o[e], "u": u[e]}, "posi": {"cell": c[ps_], "off": o[ps_], "u": u[ps_]},
+          "E": E}
+    steps = int(args.corot_time / p["dt"])
+    chunk = 100
+    snaps, recs = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with Cascade(p, state=st) as cas:
+        done = 0
+        while done < steps:
+            cas.step(chunk)
+            done += chunk
+            recs.append(cas.diag(chunk))
+            if args.save_series:
+                snaps.append(cas.fields()[0].astype(np.float32))
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    rec = {k: np.concatenate([r[k] for r in recs]) for k in recs[0]}
+    pairs = rec["n_pairs_total"]
+    first = float(rec["t"][np.argmax(pairs > 0)]) if pairs[-1] > 0 else float("nan")
+    if args.save_series:
+        np.savez_compressed(os.path.join(args.save_series, "corotating.npz"), t=rec["t"], pairs=pairs,
+                            n_elec=rec["n_elec"], n_posi=rec["n_posi"], E_absmax=rec["E_absmax"],
+                            E_map=np.array(snaps), dt_map=p["dt"] * chunk)
+    line = {"metric": B.METRIC, "value": float((rec["n_elec"] + rec["n_posi"]).sum() / el), "unit": UNIT,
+            "workload": "co-rotating frame, Section 7 parameters", "steps": steps, "seconds": el,
+            "time_of_first_pairs": first, "pairs_total": int(pairs[-1]), "peak_field": float(rec["E_absmax"].max()),
+            "particles_end": int(rec["n_elec"][-1] + rec["n_posi"][-1])}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run(args) -> int:
-    return {"batch": run_batch, "serve": run_serve, "sweep": run_sweep, "paper": run_paper}[args.workload](args)
+    return {"batch": run_batch, "serve": run_serve, "sweep": run_sweep, "paper": run_paper,
+            "corotating": run_corotating}[args.workload](args)

@@ -421,27 +421,34 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
   // QED (Section 2): threshold emission with recoil; photons appended with
   // one warp-wide scan and one global atomic per slot that has emitters
   if (OPEN) {
-    // departed particles: their indices join the species' hole list (one
-    // warp-wide scan and one atomic per warp)
+    // departed particles: their indices join their species' hole list (a
+    // warp can hold both species, so one warp-wide scan and one atomic per
+    // species present)
     const int nd = (int)departed[0] + (int)departed[1] + (int)departed[2] + (int)departed[3];
     if (__any_sync(kFull, nd > 0)) {
-      int incl = nd;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += v;
-      }
-      const int tot = __shfl_sync(kFull, incl, 31);
-      unsigned long long b0 = 0;
-      if (lane == 0) b0 = atomicAdd(&st.ctl->n_holes[s], (unsigned long long)tot);
-      b0 = __shfl_sync(kFull, b0, 0);
-      unsigned long long pos = b0 + incl - nd;
+      for (int sp = 0; sp < 2; ++sp) {
+        const int mine = (s == sp) ? nd : 0;
+        int incl = mine;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (departed[j]) {
-          if ((long long)pos < d.hole_cap) d.holes[s][pos] = base + j;
-          else set_error(st.ctl, CASCADE_ERR_CAPACITY);
-          ++pos;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int tot = __shfl_sync(kFull, incl, 31);
+        if (tot == 0) continue;
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&st.ctl->n_holes[sp], (unsigned long long)tot);
+        b0 = __shfl_sync(kFull, b0, 0);
+        if (mine == 0) continue;
+        unsigned long long pos = b0 + incl - mine;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (departed[j]) {
+            if ((long long)pos < d.hole_cap) d.holes[sp][pos] = base + j;
+            else set_error(st.ctl, CASCADE_ERR_CAPACITY);
+            ++pos;
+          }
         }
       }
     }

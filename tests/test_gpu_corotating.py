@@ -64,14 +64,15 @@ def test_open_outflow_matches_oracle(precision, tol):
     state = cold_state(nx, 0, 4, 0.0, 0.8)
     E = (np.arange(nx) + 0.5) * dx
     r_ref, r_gpu, snaps = run_pair(p, state, E, 600)
+    E_scale = np.abs(E).max()  # the field decays to ~0 once the beam has left
     if precision == "fp64":
         assert np.array_equal(r_gpu["n_posi"], r_ref["n_posi"])
     else:
         assert np.abs(r_gpu["n_posi"] - r_ref["n_posi"]).max() <= 2
     assert r_gpu["n_posi"][-1] < r_gpu["n_posi"][0] / 2
     for _, Eg, Jg, Er, Jr, gres in snaps:
-        assert np.abs(Eg - Er).max() <= tol * np.abs(Er).max()
-        assert gres <= (1e-12 if precision == "fp64" else 1e-4) * np.abs(Er).max()
+        assert np.abs(Eg - Er).max() <= tol * E_scale
+        assert gres <= (1e-12 if precision == "fp64" else 1e-4) * E_scale
 
 
 def test_departures_and_dropped_photons_are_exact():
