@@ -810,6 +810,10 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
   b->bd.work_next = b->d_work;
   b->bd.n = max_slots;
   b->bd.max_nx = max_nx;
+  {
+    const char* env = getenv("CASCADE_BATCH_PREFETCH");  // measurement override
+    b->bd.prefetch = (env && *env) ? atoi(env) : 1;
+  }
   if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return fail(cuda_fail(e, "sync"));
   *out = b;
   return CASCADE_OK;

@@ -89,6 +89,7 @@ struct BatchDev {
   unsigned long long* work_next; // next work item to hand out
   int n;                         // slots
   int max_nx;                    // largest member grid (shared-memory sizing)
+  int prefetch;                  // iterations ahead the particle kernel prefetches into L2
 };
 
 enum PushVariant {

@@ -1054,7 +1054,22 @@ __global__ void __launch_bounds__(512, MINB) k_batch_push(BatchDev b) {
     double gsum = 0.0;
     const long long nchunks = c1 - c0;
     const long long iters = (nchunks + blockDim.x - 1) / blockDim.x;
+    const int pf = b.prefetch;
     for (long long it = 0; it < iters; ++it) {
+      if (pf > 0 && lane == 0) {
+        // the warp's particles pf iterations ahead, inside this item
+        const long long chp = c0 + (it + pf) * blockDim.x + warp * 32;
+        if (chp < c1) {
+          const long long bp = chp * 4;
+          long long np = p1 - bp;
+          if (np > 128) np = 128;
+          if (np > 0) {
+            prefetch_l2(d.cell[s] + bp, (unsigned)(np * 4) & ~15u);
+            prefetch_l2(static_cast<const Real*>(d.off[s]) + bp, (unsigned)(np * sizeof(Real)) & ~15u);
+            prefetch_l2(static_cast<const Real*>(d.u[s]) + bp, (unsigned)(np * sizeof(Real)) & ~15u);
+          }
+        }
+      }
       const long long ch = c0 + it * blockDim.x + warp * 32 + lane;
       long long base = 0;
       int cnt = 0;
