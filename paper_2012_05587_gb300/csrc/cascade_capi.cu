@@ -234,7 +234,7 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
     const char* env = getenv("CASCADE_BATCH_ITEM_MULT");
     const long long mult = (env && *env) ? atoll(env) : 64;
     long long it = (mult > 0 ? mult : 64) * (long long)d.nx;
-    if (it < 16384) it = 16384;
+    if (it < 131072) it = 131072;
     d.item_size = (it + 3) & ~3LL;
   }
   if (d.open_bc) {
@@ -812,7 +812,7 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
   b->bd.max_nx = max_nx;
   {
     const char* env = getenv("CASCADE_BATCH_PREFETCH");  // measurement override
-    b->bd.prefetch = (env && *env) ? atoi(env) : 1;
+    b->bd.prefetch = (env && *env) ? atoi(env) : 0;  // measured: no gain at 2 CTAs per SM
   }
   if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return fail(cuda_fail(e, "sync"));
   *out = b;

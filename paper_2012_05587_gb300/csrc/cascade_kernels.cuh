@@ -24,6 +24,7 @@ namespace cpic {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kFieldGroups = 8;  // row groups of the field kernel (kFieldBlock / 32)
+constexpr int kBatchSmemSlots = 1024;  // batches up to this size keep the item offsets in shared memory
 // Upper bound on photons one lepton emits in one step (a step that needs more
 // is far too coarse for the model; the count is clamped).
 constexpr int kMaxPhotonsPerStep = 1 << 16;
@@ -781,7 +782,19 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(Dev d) {
     if (i < d.nx) {
       const Acc* P = static_cast<const Acc*>(d.S_part) + i;
       const size_t pitch = d.nxp;
-      for (int b = g; b < G; b += kFieldGroups) S += (double)P[(size_t)b * pitch];
+      // four independent loads in flight, added in row order
+      int b = g;
+      for (; b + 3 * kFieldGroups < G; b += 4 * kFieldGroups) {
+        const double v0 = (double)P[(size_t)b * pitch];
+        const double v1 = (double)P[(size_t)(b + kFieldGroups) * pitch];
+        const double v2 = (double)P[(size_t)(b + 2 * kFieldGroups) * pitch];
+        const double v3 = (double)P[(size_t)(b + 3 * kFieldGroups) * pitch];
+        S += v0;
+        S += v1;
+        S += v2;
+        S += v3;
+      }
+      for (; b < G; b += kFieldGroups) S += (double)P[(size_t)b * pitch];
     }
     grp[g][lane] = S;
     __syncthreads();
@@ -993,7 +1006,13 @@ __global__ void __launch_bounds__(512, MINB) k_batch_push(BatchDev b) {
   __shared__ double red[16];
   __shared__ long long s_item;
   __shared__ int s_slot;
+  __shared__ long long s_start[kBatchSmemSlots + 1];  // item offsets of the members, for the search
   const long long total = b.item_start[b.n];
+  const bool cached = b.n <= kBatchSmemSlots;
+  if (cached)
+    for (int i = threadIdx.x; i <= b.n; i += blockDim.x) s_start[i] = b.item_start[i];
+  __syncthreads();
+  const long long* starts = cached ? s_start : b.item_start;
   const size_t eb = ((size_t)b.max_nx * sizeof(Real) + 15) & ~size_t(15);
   PushState<Real, DEP> st;
   st.Es = reinterpret_cast<Real*>(smem_raw);
@@ -1008,7 +1027,7 @@ __global__ void __launch_bounds__(512, MINB) k_batch_push(BatchDev b) {
         int lo = 0, hi = b.n;  // last slot with item_start <= item
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
-          if (b.item_start[mid] <= item) lo = mid;
+          if (starts[mid] <= item) lo = mid;
           else hi = mid;
         }
         s_slot = lo;
@@ -1030,7 +1049,7 @@ __global__ void __launch_bounds__(512, MINB) k_batch_push(BatchDev b) {
     const long long N0 = ctl->n[0] + cc, N1 = ctl->n[1] + cc;
     const long long P = d.item_size;
     const long long items0 = (N0 + P - 1) / P;
-    const long long local = item - b.item_start[slot];
+    const long long local = item - starts[slot];
     const int s = local < items0 ? 0 : 1;
     const long long idx = s ? local - items0 : local;
     const long long Ns = s ? N1 : N0;
