@@ -104,6 +104,9 @@ def run_serve(args) -> int:
     reqs = W.serving_requests(args.requests, rate=args.rate, precision=prec)
     free = torch.cuda.mem_get_info()[0]
     budget = int(0.6 * free)
+    # a private stream: host reads of finished requests never wait for the batch
+    serve_stream = torch.cuda.Stream()
+    torch.cuda.set_stream(serve_stream)
     b = CascadeBatch(slots=256, precision=prec, max_nx=8192, hbm_budget=budget)
     pending = list(reqs)
     queue = []

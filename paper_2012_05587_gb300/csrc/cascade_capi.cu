@@ -327,9 +327,17 @@ int set_counts(cascade_t* h, long long ne, long long np) {
   return CASCADE_OK;
 }
 
-int read_ctl(cascade_t* h, Ctl* c) {
+// Copies to the host go through the handle's own stream, so they never wait
+// for work queued on other streams.
+int d2h(cascade_t* h, void* dst, const void* src, size_t bytes) {
+  CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  CUDA_TRY(cudaMemcpy(c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  return CASCADE_OK;
+}
+
+int read_ctl(cascade_t* h, Ctl* c) {
+  int rc = d2h(h, c, h->d.ctl, sizeof(Ctl));
+  if (rc) return rc;
   if (c->err && !h->sticky) h->sticky = c->err;
   return CASCADE_OK;
 }
@@ -469,12 +477,13 @@ int cascade_diag(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t* n
     const long long slot = (first + done) % h->d.ring_n;
     long long run = h->d.ring_n - slot;
     if (run > n - done) run = n - done;
-    CUDA_TRY(cudaMemcpy(host_out + done, h->d.ring + slot, sizeof(cascade_diag_t) * run, cudaMemcpyDeviceToHost));
+    rc = d2h(h, host_out + done, h->d.ring + slot, sizeof(cascade_diag_t) * run);
+    if (rc) return rc;
     done += run;
   }
   if (n_out) *n_out = (int32_t)n;
-  if (E_host) CUDA_TRY(cudaMemcpy(E_host, h->d.E, sizeof(double) * h->d.nx, cudaMemcpyDeviceToHost));
-  if (J_host) CUDA_TRY(cudaMemcpy(J_host, h->d.J, sizeof(double) * h->d.nx, cudaMemcpyDeviceToHost));
+  if (E_host && (rc = d2h(h, E_host, h->d.E, sizeof(double) * h->d.nx))) return rc;
+  if (J_host && (rc = d2h(h, J_host, h->d.J, sizeof(double) * h->d.nx))) return rc;
   return h->sticky;
 }
 
@@ -967,12 +976,20 @@ int cascade_batch_poll(cascade_batch_t* b, int32_t* done_slots, int32_t max, int
   return CASCADE_OK;
 }
 
+// A member reported finished is skipped by every later batch kernel, so its
+// state can be read, or its memory released, without waiting for the batch.
+int batch_settle(cascade_batch_t* b, int slot) {
+  if (b->reported[slot]) return CASCADE_OK;
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return CASCADE_OK;
+}
+
 int cascade_batch_diag(cascade_batch_t* b, int32_t slot, cascade_diag_t* host_out, int32_t max, int32_t* n_out,
                        double* E_host, double* J_host) {
   int rc = batch_member_check(b, slot);
   if (rc) return rc;
   cudaSetDevice(b->device);
-  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  if ((rc = batch_settle(b, slot))) return rc;
   return cascade_diag(b->members[slot], host_out, max, n_out, E_host, J_host);
 }
 
@@ -981,7 +998,7 @@ int cascade_batch_counts(cascade_batch_t* b, int32_t slot, int64_t* n_elec, int6
   int rc = batch_member_check(b, slot);
   if (rc) return rc;
   cudaSetDevice(b->device);
-  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  if ((rc = batch_settle(b, slot))) return rc;
   return cascade_counts(b->members[slot], n_elec, n_posi, n_photon, step);
 }
 
@@ -989,9 +1006,13 @@ int cascade_batch_release(cascade_batch_t* b, int32_t slot) {
   int rc = batch_member_check(b, slot);
   if (rc) return rc;
   cudaSetDevice(b->device);
-  CUDA_TRY(cudaStreamSynchronize(b->stream));
-  b->h_set[slot] = 0;
-  CUDA_TRY(cudaMemcpy(b->d_remaining + slot, b->h_set + slot, sizeof(long long), cudaMemcpyHostToDevice));
+  if (!b->reported[slot]) {
+    // still running: stop it behind the queued work, then wait for that work
+    b->h_set[slot] = 0;
+    CUDA_TRY(cudaMemcpyAsync(b->d_remaining + slot, b->h_set + slot, sizeof(long long), cudaMemcpyHostToDevice,
+                             b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+  }
   cascade_t* h = b->members[slot];
   b->used -= h->bytes;
   b->members[slot] = nullptr;
