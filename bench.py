@@ -63,12 +63,13 @@ def parse():
                          "errors of the ensemble diagnostics")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=3000)
-    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--fp64-sample", type=int, default=8, help="cascades run one at a time in FP64 for comparison")
     ap.add_argument("--paper-time", type=float, default=12.0, help="paper workload: simulated time (1/omega_p)")
     ap.add_argument("--save-series", default="", help="paper/corotating workloads: directory for the series")
     ap.add_argument("--corot-time", type=float, default=200.0, help="corotating workload: simulated time")
+    ap.add_argument("--sweep-seeds", type=int, default=8, help="sweep workload: seeds averaged per configuration")
     return ap.parse_args()
 
 
@@ -134,10 +135,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_slice(steps_prep: int, steps_timed: int):
+def oracle_slice(steps_prep: int, steps_timed: int, multicore: bool = False):
     """FP64 oracle on an Nx = 512 slice of the large cascade (same dx, dt,
     ppc, E0, gamma_thr, eps_gamma, l_pp).  Returns particle-steps/s of the
-    timed steps and what was timed."""
+    timed steps, the particle-steps, the seconds, the threads used and what was
+    timed.  ``multicore`` runs the OpenMP build of the same source on every
+    host core."""
     import oracle
     from paper_2012_05587_gb300 import workloads as W
 
@@ -145,15 +148,24 @@ def oracle_slice(steps_prep: int, steps_timed: int):
     p = {k: v for k, v in p.items() if k not in ("precision", "steps")}
     p["nx"] = 512
     p["particle_cap"] = 1 << 26
-    o = oracle.Oracle(p)
+    lib = None
+    threads = 1
+    if multicore:
+        lib = oracle.build_multicore()
+        threads = os.cpu_count() or 1
+        oracle._load(lib).orc_set_threads(threads)
+        threads = int(oracle._load(lib).orc_threads())
+    o = oracle.Oracle(p, lib_path=lib)
     if steps_prep:
         o.step(steps_prep)
     t0 = time.perf_counter()
     d = o.step(steps_timed)
     el = time.perf_counter() - t0
     ps = float((d["n_elec"] + d["n_posi"]).sum())
-    return ps / el, ps, el, (f"FP64 oracle, 1 thread, Nx=512 slice of the large cascade (64+64 per cell), "
-                             f"steps {steps_prep}-{steps_prep + steps_timed}, {ps:.3g} particle-steps in {el:.1f} s")
+    what = "multi-core (OpenMP) build" if multicore else "plain build"
+    return ps / el, ps, el, threads, (f"FP64 oracle, {what}, {threads} thread(s), Nx=512 slice of the large cascade "
+                                      f"(64+64 per cell), steps {steps_prep}-{steps_prep + steps_timed}, "
+                                      f"{ps:.3g} particle-steps in {el:.1f} s")
 
 
 def aggregate_over_ranks(ms: float, particle_steps: float, device: str = "cuda"):
@@ -289,10 +301,15 @@ def main():
         e2e = e2e_run(c, p, args.steps, stream, barrier)
     c.close()
 
-    cpu = None
+    cpu = cpu_mc = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, psx, el, sample = oracle_slice(150, 60)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        v, psx, el, nt, sample = oracle_slice(150, 60)
+        cpu = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": sample}
+        try:
+            v, psx, el, nt, sample = oracle_slice(150, 60, multicore=True)
+            cpu_mc = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle (OpenMP build)", "sample": sample}
+        except Exception as e:  # no OpenMP runtime on the host
+            cpu_mc = {"unavailable": str(e).splitlines()[0]}
 
     if rank == 0:
         line = {
@@ -309,6 +326,7 @@ def main():
                        "l2": "inputs larger than L2 (particle state >> 129 MB)"},
             "roofline": roof,
             "cpu_baseline": cpu,
+            "cpu_multicore": cpu_mc,
             "e2e": e2e,
             "gpu_launches": tim["kernels_launched"] * world,
             "clocks": clocks,

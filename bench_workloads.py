@@ -172,30 +172,39 @@ def run_serve(args) -> int:
 
 
 def run_sweep(args) -> int:
+    """Precision sweep: for each (E0, gamma_thr) the ensemble diagnostics of
+    FP32-mixed and FP32-mixed-fine runs, averaged over seeds, against the same
+    average of all-FP64 runs (relative errors per diagnostic)."""
     from paper_2012_05587_gb300 import Cascade, CascadeError, analysis, workloads as W
 
     rows = []
-    for p in W.precision_sweep():
-        steps = p["steps"]
-        row = {"E0": p["E0"], "gamma_thr": p["gamma_thr"], "dt": p["dt"]}
-        res = {}
-        for prec in ("fp64", "fp32", "fp32_fine"):
-            q = dict(p, precision=prec)
-            if prec == "fp64":
-                q["particle_cap"] = 120_000_000
-            try:
-                with Cascade(q) as c:
-                    c.step(steps)
-                    rec = c.diag(steps)
-                res[prec] = analysis.ensemble(rec)
-            except CascadeError as e:
-                res[prec] = {"error": str(e).split(":")[1].strip() if ":" in str(e) else str(e)}
-        row["fp64"] = res["fp64"]
-        for prec in ("fp32", "fp32_fine"):
-            if "error" in res[prec] or "error" in res["fp64"]:
-                row[prec] = res[prec]
-            else:
-                row[prec + "_rel_err"] = analysis.relative_errors(res[prec], res["fp64"])
+    seeds = list(range(args.sweep_seeds))
+    for idx in range(9):
+        res = {"fp64": [], "fp32": [], "fp32_fine": []}
+        errs = {}
+        p0 = None
+        for run in seeds:
+            p = W.precision_sweep(run=run)[idx]
+            p0 = p
+            for prec in res:
+                q = dict(p, precision=prec)
+                if prec == "fp64":
+                    q["particle_cap"] = 120_000_000
+                try:
+                    with Cascade(q) as c:
+                        c.step(p["steps"])
+                        rec = c.diag(p["steps"])
+                    res[prec].append(analysis.ensemble(rec))
+                except CascadeError as e:
+                    errs[prec] = str(e).split(":")[1].strip() if ":" in str(e) else str(e)
+        row = {"E0": p0["E0"], "gamma_thr": p0["gamma_thr"], "dt": p0["dt"], "seeds": len(seeds)}
+        if errs:
+            row["errors"] = errs
+        else:
+            mean = {k: {f: float(np.nanmean([r[f] for r in v])) for f in v[0]} for k, v in res.items()}
+            row["fp64_mean"] = mean["fp64"]
+            row["fp32_rel_err"] = analysis.relative_errors(mean["fp32"], mean["fp64"])
+            row["fp32_fine_rel_err"] = analysis.relative_errors(mean["fp32_fine"], mean["fp64"])
         rows.append(row)
         print(json.dumps({"sweep_row": row}), flush=True)
     line = {"metric": B.METRIC, "value": None, "unit": UNIT, "workload": "precision sweep", "rows": rows}

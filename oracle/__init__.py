@@ -24,12 +24,16 @@ _lock = threading.Lock()
 _libs: dict = {}
 
 
-def compile_source(src: str, out: str) -> str:
-    """Compile an oracle source file into a shared library (gcc, no FMA contraction)."""
+_LIB_MC = os.path.join(_HERE, "liboracle_mc.so")
+
+
+def compile_source(src: str, out: str, openmp: bool = False) -> str:
+    """Compile an oracle source file into a shared library (gcc, no FMA
+    contraction); ``openmp`` gives the multi-core build of the same source."""
     tmp = out + f".tmp{os.getpid()}"
     subprocess.check_call([
         "gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-        src, "-o", tmp, "-lm",
+        *(["-fopenmp"] if openmp else []), src, "-o", tmp, "-lm",
     ])
     os.replace(tmp, out)
     return out
@@ -40,6 +44,14 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         compile_source(_SRC, _LIB)
     return _LIB
+
+
+def build_multicore(force: bool = False) -> str:
+    """Compile the multi-core (OpenMP) build into ``oracle/liboracle_mc.so``;
+    it is used only to time the oracle on all host cores."""
+    if force or not os.path.exists(_LIB_MC) or os.path.getmtime(_LIB_MC) < os.path.getmtime(_SRC):
+        compile_source(_SRC, _LIB_MC, openmp=True)
+    return _LIB_MC
 
 
 SOURCE = _SRC
@@ -103,6 +115,10 @@ def _load(path: str | None = None):
             lib.orc_seed_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64,
                                              P(ctypes.c_double), P(ctypes.c_double)]
             lib.orc_seed_normals.restype = None
+            lib.orc_threads.argtypes = []
+            lib.orc_threads.restype = ctypes.c_int32
+            lib.orc_set_threads.argtypes = [ctypes.c_int32]
+            lib.orc_set_threads.restype = None
             _libs[key] = lib
     return _libs[key]
 

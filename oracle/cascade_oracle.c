@@ -44,11 +44,22 @@
  *
  * Floating point: plain double arithmetic, evaluated in source order; build
  * with -ffp-contract=off so no multiply-add is fused.
+ *
+ * Multi-core build (-fopenmp, used only to time the CPU on all host cores):
+ * the particle loops of step 2 and of the diagnostics run over contiguous
+ * blocks of particles, one per thread; each thread sums its deposit into a
+ * row of its own and the rows are added in thread order.  Photon creation,
+ * emission and removal stay sequential, so every list keeps its order.  With
+ * one thread the result is bit-identical to the plain build; with more, the
+ * sums of J, rho and U_K change order (round-off only).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------- */
 /* Parameters and per-step diagnostics (oracle's own layout).                 */
@@ -104,6 +115,8 @@ typedef struct {
   int8_t *ph_dir;
 
   double *E, *J, *S, *rho_dx;
+  double *rows;        /* multi-core build: n_rows x nx per-thread sums */
+  int32_t n_rows;
   int64_t pairs_total, emit_multi;
   int error;
 } orc_sim;
@@ -241,7 +254,7 @@ void orc_destroy(orc_sim* s) {
   if (!s) return;
   free(s->cell); free(s->off); free(s->u); free(s->gam); free(s->q);
   free(s->ph_conv_step); free(s->ph_cell); free(s->ph_off); free(s->ph_dir);
-  free(s->E); free(s->J); free(s->S); free(s->rho_dx);
+  free(s->E); free(s->J); free(s->S); free(s->rho_dx); free(s->rows);
   free(s);
 }
 
@@ -319,58 +332,98 @@ static void convert_photons(orc_sim* s) {
   if (!s->error) s->nph = kept;
 }
 
-static void push_move_deposit(orc_sim* s) {
+/* Step 2 for particle p: gather, push, move, and deposit into S. */
+static void move_particle(orc_sim* s, int64_t p, double* S) {
   const int32_t nx = s->p.nx;
   const int open = s->p.open_bc;
   const double dt = s->p.dt, dtdx = s->dtdx;
-  for (int32_t i = 0; i < nx; ++i) s->S[i] = 0.0;
-  for (int64_t p = 0; p < s->np; ++p) {
-    const double q = (double)s->q[p];
-    int32_t c = s->cell[p];
-    double o = s->off[p];
-    /* gather: linear interpolation between the two edges bracketing x (open
-     * boundaries: beyond the outermost edges the field is that edge's) */
-    int32_t ia, ib;
-    double w;
-    if (o >= 0.5) { ia = c; ib = (c + 1 == nx) ? (open ? nx - 1 : 0) : c + 1; w = o - 0.5; }
-    else          { ia = (c == 0) ? (open ? 0 : nx - 1) : c - 1; ib = c; w = o + 0.5; }
-    double Ep = (1.0 - w) * s->E[ia] + w * s->E[ib];
-    /* push: du/dt = q E */
-    double u = s->u[p] + q * dt * Ep;
-    double g = sqrt(1.0 + u * u);
-    /* move: dx/dt = u / gamma, in cell units */
-    double d = u / g * dtdx;
-    double o2 = o + d;
-    int32_t c2 = c;
-    /* deposit: charge-conserving current of the CIC shape, one term per
-     * sub-segment between nodes; sum q * (offset change) per edge */
-    if (o2 >= 1.0) {
-      s->S[c] += q * (1.0 - o);
-      if (open && c + 1 == nx) {
-        c2 = -1;  /* left through x = L: the part inside is deposited */
-      } else {
-        c2 = (c + 1 == nx) ? 0 : c + 1;
-        o2 = o2 - 1.0;
-        s->S[c2] += q * o2;
-      }
-    } else if (o2 < 0.0) {
-      s->S[c] += q * (0.0 - o);
-      if (open && c == 0) {
-        c2 = -1;  /* left through x = 0 */
-      } else {
-        c2 = (c == 0) ? nx - 1 : c - 1;
-        o2 = o2 + 1.0;
-        s->S[c2] += q * (o2 - 1.0);
-        if (o2 >= 1.0) { o2 = 0.0; c2 = c; }  /* rounding landed on the node itself */
-      }
+  const double q = (double)s->q[p];
+  int32_t c = s->cell[p];
+  double o = s->off[p];
+  /* gather: linear interpolation between the two edges bracketing x (open
+   * boundaries: beyond the outermost edges the field is that edge's) */
+  int32_t ia, ib;
+  double w;
+  if (o >= 0.5) { ia = c; ib = (c + 1 == nx) ? (open ? nx - 1 : 0) : c + 1; w = o - 0.5; }
+  else          { ia = (c == 0) ? (open ? 0 : nx - 1) : c - 1; ib = c; w = o + 0.5; }
+  double Ep = (1.0 - w) * s->E[ia] + w * s->E[ib];
+  /* push: du/dt = q E */
+  double u = s->u[p] + q * dt * Ep;
+  double g = sqrt(1.0 + u * u);
+  /* move: dx/dt = u / gamma, in cell units */
+  double d = u / g * dtdx;
+  double o2 = o + d;
+  int32_t c2 = c;
+  /* deposit: charge-conserving current of the CIC shape, one term per
+   * sub-segment between nodes; sum q * (offset change) per edge */
+  if (o2 >= 1.0) {
+    S[c] += q * (1.0 - o);
+    if (open && c + 1 == nx) {
+      c2 = -1;  /* left through x = L: the part inside is deposited */
     } else {
-      s->S[c] += q * (o2 - o);
+      c2 = (c + 1 == nx) ? 0 : c + 1;
+      o2 = o2 - 1.0;
+      S[c2] += q * o2;
     }
-    s->cell[p] = c2;
-    s->off[p] = o2;
-    s->u[p] = u;
-    s->gam[p] = g;
+  } else if (o2 < 0.0) {
+    S[c] += q * (0.0 - o);
+    if (open && c == 0) {
+      c2 = -1;  /* left through x = 0 */
+    } else {
+      c2 = (c == 0) ? nx - 1 : c - 1;
+      o2 = o2 + 1.0;
+      S[c2] += q * (o2 - 1.0);
+      if (o2 >= 1.0) { o2 = 0.0; c2 = c; }  /* rounding landed on the node itself */
+    }
+  } else {
+    S[c] += q * (o2 - o);
   }
+  s->cell[p] = c2;
+  s->off[p] = o2;
+  s->u[p] = u;
+  s->gam[p] = g;
+}
+
+#ifdef _OPENMP
+/* Multi-core build: n_rows x nx scratch for per-thread sums. */
+static double* thread_rows(orc_sim* s) {
+  int32_t nt = (int32_t)omp_get_max_threads();
+  if (nt > s->n_rows) {
+    free(s->rows);
+    s->rows = malloc((size_t)nt * (size_t)s->p.nx * sizeof(double));
+    s->n_rows = s->rows ? nt : 0;
+  }
+  return s->rows;
+}
+
+/* Adds the first nt rows into out, in row order. */
+static void sum_rows(const orc_sim* s, int32_t nt, double* out) {
+  for (int32_t i = 0; i < s->p.nx; ++i) out[i] = 0.0;
+  for (int32_t t = 0; t < nt; ++t)
+    for (int32_t i = 0; i < s->p.nx; ++i) out[i] += s->rows[(size_t)t * s->p.nx + i];
+}
+#endif
+
+static void push_move_deposit(orc_sim* s) {
+  const int32_t nx = s->p.nx;
+#ifdef _OPENMP
+  if (thread_rows(s)) {
+    int32_t nt = 1;
+#pragma omp parallel
+    {
+      double* S = s->rows + (size_t)omp_get_thread_num() * nx;
+      for (int32_t i = 0; i < nx; ++i) S[i] = 0.0;
+#pragma omp single
+      nt = (int32_t)omp_get_num_threads();
+#pragma omp for schedule(static)
+      for (int64_t p = 0; p < s->np; ++p) move_particle(s, p, S);
+    }
+    sum_rows(s, nt, s->S);
+    return;
+  }
+#endif
+  for (int32_t i = 0; i < nx; ++i) s->S[i] = 0.0;
+  for (int64_t p = 0; p < s->np; ++p) move_particle(s, p, s->S);
 }
 
 /* Open boundaries: particles that left (cell -1) are removed, keeping the
@@ -437,16 +490,36 @@ static void qed_emission(orc_sim* s) {
   }
 }
 
+/* CIC charge of particle p into rho_dx (node cell and cell + 1). */
+static void particle_charge(const orc_sim* s, int64_t p, double* rho_dx) {
+  const int32_t nx = s->p.nx;
+  int32_t c = s->cell[p];
+  double qw = (double)s->q[p] * s->w;
+  rho_dx[c] += qw * (1.0 - s->off[p]);
+  if (c + 1 < nx) rho_dx[c + 1] += qw * s->off[p];
+  else if (!s->p.open_bc) rho_dx[0] += qw * s->off[p];  /* periodic node nx = node 0 */
+}
+
 static void charge_density(orc_sim* s) {
   const int32_t nx = s->p.nx;
-  for (int32_t i = 0; i < nx; ++i) s->rho_dx[i] = 0.0;
-  for (int64_t p = 0; p < s->np; ++p) {
-    int32_t c = s->cell[p];
-    double qw = (double)s->q[p] * s->w;
-    s->rho_dx[c] += qw * (1.0 - s->off[p]);
-    if (c + 1 < nx) s->rho_dx[c + 1] += qw * s->off[p];
-    else if (!s->p.open_bc) s->rho_dx[0] += qw * s->off[p];  /* periodic node nx = node 0 */
+#ifdef _OPENMP
+  if (thread_rows(s)) {
+    int32_t nt = 1;
+#pragma omp parallel
+    {
+      double* R = s->rows + (size_t)omp_get_thread_num() * nx;
+      for (int32_t i = 0; i < nx; ++i) R[i] = 0.0;
+#pragma omp single
+      nt = (int32_t)omp_get_num_threads();
+#pragma omp for schedule(static)
+      for (int64_t p = 0; p < s->np; ++p) particle_charge(s, p, R);
+    }
+    sum_rows(s, nt, s->rho_dx);
+    return;
   }
+#endif
+  for (int32_t i = 0; i < nx; ++i) s->rho_dx[i] = 0.0;
+  for (int64_t p = 0; p < s->np; ++p) particle_charge(s, p, s->rho_dx);
 }
 
 static void diagnostics(orc_sim* s, orc_diag* d) {
@@ -459,6 +532,9 @@ static void diagnostics(orc_sim* s, orc_diag* d) {
     if (a > amax) amax = a;
     ue += 0.5 * s->E[i] * s->E[i] * s->p.dx;
   }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : uk)
+#endif
   for (int64_t p = 0; p < s->np; ++p) uk += s->w * s->gam[p];
   /* Gauss on node i between edges i-1/2 and i+1/2: E[i] - E[i-1] =
    * dx (rho_i - rho_GJ); with open boundaries only the interior nodes */
@@ -533,3 +609,21 @@ void orc_get_photons(const orc_sim* s, int64_t* conv_step, int32_t* cell, double
 
 /* Current diagnostics without stepping (state at the present step). */
 void orc_diag_now(orc_sim* s, orc_diag* d) { diagnostics(s, d); }
+
+/* Threads the particle loops use: 1 in the plain build. */
+int32_t orc_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* Multi-core build: sets the thread count (no effect in the plain build). */
+void orc_set_threads(int32_t n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

@@ -51,9 +51,9 @@ MUTANTS = [
     ("gather_left_weight", "ib = c; w = o + 0.5; }", "ib = c; w = 0.5 - o; }"),
     ("push_charge_dropped", "double u = s->u[p] + q * dt * Ep;", "double u = s->u[p] + dt * Ep;"),
     ("move_uses_momentum", "double d = u / g * dtdx;", "double d = u * dtdx;"),
-    ("deposit_sign", "s->S[c] += q * (o2 - o);", "s->S[c] += q * (o - o2);"),
-    ("deposit_crossing_edge", "s->S[c2] += q * o2;", "s->S[c] += q * o2;"),
-    ("deposit_backward_term", "s->S[c2] += q * (o2 - 1.0);", "s->S[c2] += q * (1.0 - o2);"),
+    ("deposit_sign", "S[c] += q * (o2 - o);", "S[c] += q * (o - o2);"),
+    ("deposit_crossing_edge", "S[c2] += q * o2;", "S[c] += q * o2;"),
+    ("deposit_backward_term", "S[c2] += q * (o2 - 1.0);", "S[c2] += q * (1.0 - o2);"),
     ("ampere_sign", "s->E[i] = s->E[i] - dt * (s->J[i] - s->p.j_m);", "s->E[i] = s->E[i] + dt * (s->J[i] - s->p.j_m);"),
     ("current_scale", "s->jscale = p->n0 * p->dx / ((double)p->ppc * p->dt);",
      "s->jscale = 2.0 * p->n0 * p->dx / ((double)p->ppc * p->dt);"),
@@ -70,7 +70,7 @@ MUTANTS = [
      "s->E[i] = s->E[i] - dt * (s->J[i] + s->p.j_m);"),
     ("background_charge_sign", "(s->rho_dx[i] - s->p.rho_gj * s->p.dx)", "(s->rho_dx[i] + s->p.rho_gj * s->p.dx)"),
     ("open_gather_wraps", "ia = (c == 0) ? (open ? 0 : nx - 1) : c - 1;", "ia = (c == 0) ? nx - 1 : c - 1;"),
-    ("departing_deposit", "s->S[c] += q * (1.0 - o);", "s->S[c] += q * (0.5 - o);"),
+    ("departing_deposit", "S[c] += q * (1.0 - o);", "S[c] += q * (0.5 - o);"),
     ("photon_outside_kept", "if (s->p.open_bc && (ci < 0 || ci >= s->p.nx)) continue;", "if (0) continue;"),
 ]
 
