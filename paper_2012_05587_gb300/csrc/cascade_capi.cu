@@ -224,18 +224,9 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
     if (!d.S_part) return CASCADE_ERR_OOM;
   } else {
     // global FP64 current: the single-cascade fallback variants and every
-    // batch member (its work items add their currents here)
+    // batch member (each CTA adds its share of the current here)
     d.S_glob = static_cast<double*>(h->dalloc(sizeof(double) * d.nx));
     if (!d.S_glob) return CASCADE_ERR_OOM;
-  }
-  {
-    // batched work item: enough particles that staging E and flushing the
-    // current (about 2 nx words each) stay a small part of the item's work
-    const char* env = getenv("CASCADE_BATCH_ITEM_MULT");
-    const long long mult = (env && *env) ? atoll(env) : 64;
-    long long it = (mult > 0 ? mult : 64) * (long long)d.nx;
-    if (it < 131072) it = 131072;
-    d.item_size = (it + 3) & ~3LL;
   }
   if (d.open_bc) {
     // departures per step are bounded by the particles next to the boundaries
@@ -675,7 +666,6 @@ struct cascade_batch {
   Dev* d_devs = nullptr;
   long long* d_remaining = nullptr;
   long long* d_item_start = nullptr;
-  unsigned long long* d_work = nullptr;
   void* d_block = nullptr;             // one allocation holding the tables
   // pinned host mirrors
   Dev* h_devs = nullptr;
@@ -791,14 +781,13 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
   const size_t b_devs = (sizeof(Dev) * n + 255) & ~size_t(255);
   const size_t b_rem = (sizeof(long long) * n + 255) & ~size_t(255);
   const size_t b_items = (sizeof(long long) * (n + 1) + 255) & ~size_t(255);
-  const size_t total = b_devs + b_rem + b_items + 256;
+  const size_t total = b_devs + b_rem + b_items;
   e = cudaMalloc(&b->d_block, total);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc batch tables"));
   char* base = static_cast<char*>(b->d_block);
   b->d_devs = reinterpret_cast<Dev*>(base);
   b->d_remaining = reinterpret_cast<long long*>(base + b_devs);
   b->d_item_start = reinterpret_cast<long long*>(base + b_devs + b_rem);
-  b->d_work = reinterpret_cast<unsigned long long*>(base + b_devs + b_rem + b_items);
   if ((e = cudaMemsetAsync(b->d_block, 0, total, b->stream)) != cudaSuccess) return fail(cuda_fail(e, "memset"));
   if ((e = cudaMallocHost(&b->h_devs, sizeof(Dev) * n)) != cudaSuccess) return fail(cuda_fail(e, "host mirror"));
   memset(b->h_devs, 0, sizeof(Dev) * n);
@@ -816,12 +805,13 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
   b->bd.devs = b->d_devs;
   b->bd.remaining = b->d_remaining;
   b->bd.item_start = b->d_item_start;
-  b->bd.work_next = b->d_work;
   b->bd.n = max_slots;
   b->bd.max_nx = max_nx;
   {
     const char* env = getenv("CASCADE_BATCH_PREFETCH");  // measurement override
-    b->bd.prefetch = (env && *env) ? atoi(env) : 0;  // measured: no gain at 2 CTAs per SM
+    b->bd.prefetch = (env && *env) ? atoi(env) : 1;  // measured: one iteration ahead is best
+    const char* mc = getenv("CASCADE_BATCH_MEMBER_COST");  // measurement override
+    b->bd.member_cost = (mc && *mc) ? atoll(mc) : 1024;  // measured: 256 to 4096 perform alike
   }
   if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return fail(cuda_fail(e, "sync"));
   *out = b;

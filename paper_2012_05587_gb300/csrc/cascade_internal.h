@@ -78,18 +78,17 @@ struct Dev {
   long long* hole_a[2];// holes below the new count
   long long* hole_b[2];// live particles at or above the new count
   long long min_per_cta;  // particles per active CTA before another CTA is woken
-  long long item_size;    // batched kernels: particles per work item (multiple of 4)
 };
 
 // A batch of cascades advanced together (one launch per kernel per step).
 struct BatchDev {
   const Dev* devs;               // [n] member descriptors
   long long* remaining;          // [n] steps left per member; 0 = idle or empty slot
-  long long* item_start;         // [n + 1] first work item of each member in this step
-  unsigned long long* work_next; // next work item to hand out
+  long long* item_start;         // [n + 1] exclusive scan of the members' work units (cost) this step
   int n;                         // slots
   int max_nx;                    // largest member grid (shared-memory sizing)
   int prefetch;                  // iterations ahead the particle kernel prefetches into L2
+  long long member_cost;         // fixed cost of a member in the partition, in 4-particle chunks
 };
 
 enum PushVariant {

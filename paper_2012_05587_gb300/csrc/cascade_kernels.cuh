@@ -945,7 +945,17 @@ __global__ void k_batch_convert(BatchDev b) {
   }
 }
 
-// Work items of every active member (exclusive scan over the slots).
+// Work units of one active member this step: its 4-particle chunks plus a
+// fixed share standing for staging E and flushing the current (member_cost +
+// nx / 4 chunks), so that contiguous ranges of equal cost take about equal
+// time.
+__device__ __forceinline__ long long batch_units(const BatchDev& b, const Dev& d) {
+  const long long cc = d.ctl->conv_count;
+  const long long N0 = d.ctl->n[0] + cc, N1 = d.ctl->n[1] + cc;
+  return ((N0 + 3) >> 2) + ((N1 + 3) >> 2) + b.member_cost + (d.nx >> 2);
+}
+
+// Exclusive scan of the members' work units over the slots.
 template <class Real>
 __global__ void __launch_bounds__(1024) k_batch_plan(BatchDev b) {
   __shared__ long long warp_tot[32];
@@ -953,14 +963,8 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchDev b) {
   const int lo = threadIdx.x * per;
   const int hi = min(lo + per, b.n);
   long long mine = 0;
-  for (int i = lo; i < hi; ++i) {
-    if (b.remaining[i] > 0) {
-      const Dev& d = b.devs[i];
-      const long long cc = d.ctl->conv_count;
-      const long long P = d.item_size;
-      mine += (d.ctl->n[0] + cc + P - 1) / P + (d.ctl->n[1] + cc + P - 1) / P;
-    }
-  }
+  for (int i = lo; i < hi; ++i)
+    if (b.remaining[i] > 0) mine += batch_units(b, b.devs[i]);
   // block-wide exclusive scan of the per-thread totals
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long incl = mine;
@@ -985,29 +989,113 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchDev b) {
   long long start = warp_tot[warp] + incl - mine;
   for (int i = lo; i < hi; ++i) {
     b.item_start[i] = start;
-    if (b.remaining[i] > 0) {
-      const Dev& d = b.devs[i];
-      const long long cc = d.ctl->conv_count;
-      const long long P = d.item_size;
-      start += (d.ctl->n[0] + cc + P - 1) / P + (d.ctl->n[1] + cc + P - 1) / P;
-    }
+    if (b.remaining[i] > 0) start += batch_units(b, b.devs[i]);
   }
-  if (threadIdx.x == blockDim.x - 1) {
-    b.item_start[b.n] = warp_tot[warp] + incl;
-    *b.work_next = 0ull;
-  }
+  if (threadIdx.x == blockDim.x - 1) b.item_start[b.n] = warp_tot[warp] + incl;
 }
 
+// Chunks [a, e) of member `slot` (species 0's chunks first, then species
+// 1's), clipped to the member's chunk count: copy its descriptor, stage its E
+// and clear the accumulator, advance the particles, then add the CTA's sum of
+// gamma and current to the member's FP64 totals with global atomics.
+template <class Real, int DEP>
+__device__ __forceinline__ void batch_range(const BatchDev& b, Dev& sd, PushState<Real, DEP>& st, double* red,
+                                            int slot, long long a, long long e) {
+  typedef typename AccOf<Real, DEP>::type Acc;
+  {
+    const long long* src = reinterpret_cast<const long long*>(b.devs + slot);
+    long long* dst = reinterpret_cast<long long*>(&sd);
+    for (int w = threadIdx.x; w < (int)(sizeof(Dev) / 8); w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
+  const Dev& d = sd;
+  Ctl* ctl = d.ctl;
+  const long long cc = ctl->conv_count;
+  const long long N0 = ctl->n[0] + cc, N1 = ctl->n[1] + cc;
+  const long long C0 = (N0 + 3) >> 2, C = C0 + ((N1 + 3) >> 2);
+  if (e > C) e = C;
+  if (a >= e) {
+    __syncthreads();  // every thread has read sd before the next member overwrites it
+    return;
+  }
+  const int nx = d.nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    st.Es[i] = (Real)d.E[i];
+    st.Ss[i] = Acc(0);
+    if (DEP == 4) st.Ls[i] = 0;
+  }
+  st.ctl = ctl;
+  st.ph_tail = ctl->ph_tail;
+  st.room = d.ph_cap - (st.ph_tail - ctl->conv_end);
+  st.ph_mask = d.ph_cap - 1;
+  set_scales<Real, DEP>(st, (double)((e - a) * 4), d.dtdx);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double gsum = 0.0;
+  const long long iters = (e - a + blockDim.x - 1) / blockDim.x;
+  const int pf = b.prefetch;
+  for (long long it = 0; it < iters; ++it) {
+    if (pf > 0 && lane == 0) {
+      // the warp's particles pf iterations ahead, inside this range
+      const long long chp = a + (it + pf) * blockDim.x + warp * 32;
+      if (chp < e) {
+        const int sp = chp < C0 ? 0 : 1;
+        const long long bp = (chp - (sp ? C0 : 0)) * 4;
+        long long np = d.cap4 - bp;  // stay inside the allocation
+        if (np > 128) np = 128;
+        if (np > 0) {
+          prefetch_l2(d.cell[sp] + bp, (unsigned)(np * 4) & ~15u);
+          prefetch_l2(static_cast<const Real*>(d.off[sp]) + bp, (unsigned)(np * sizeof(Real)) & ~15u);
+          prefetch_l2(static_cast<const Real*>(d.u[sp]) + bp, (unsigned)(np * sizeof(Real)) & ~15u);
+        }
+      }
+    }
+    const long long ch = a + it * blockDim.x + warp * 32 + lane;
+    int s = 0, cnt = 0;
+    long long base = 0;
+    if (ch < e) {
+      s = ch < C0 ? 0 : 1;
+      base = (ch - (s ? C0 : 0)) * 4;
+      cnt = (int)min(4LL, (s ? N1 : N0) - base);
+    }
+    gsum += (double)process4<Real, kSmemESmemS, DEP, true, false>(d, st, s, base, cnt, lane);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gsum += __shfl_down_sync(kFull, gsum, o);
+  if (lane == 0) red[warp] = gsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    atomicAdd(d.uk_part, v);
+  }
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    double v;
+    if (DEP == 1) v = (double)st.Ss[i] * (double)st.fx_inv;
+    else if (DEP == 4) v = (double)st.Ss[i] * (double)st.fx_inv + (double)st.Ls[i] * (double)st.lo_inv;
+    else v = (double)st.Ss[i];
+    if (v != 0.0) atomicAdd(d.S_glob + i, v);
+  }
+  __syncthreads();
+}
+
+// CTA k takes the k-th of gridDim.x equal parts of the members' total cost
+// (the exclusive scan in item_start): a contiguous run of chunks that changes
+// member only at member boundaries, so each CTA stages a member's E and
+// flushes its current once per launch, and its particles stream through in
+// order (prefetched into L2 ahead of use).
 template <class Real, int DEP, int MINB>
 __global__ void __launch_bounds__(512, MINB) k_batch_push(BatchDev b) {
   typedef typename AccOf<Real, DEP>::type Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) Dev sd;
   __shared__ double red[16];
-  __shared__ long long s_item;
-  __shared__ int s_slot;
-  __shared__ long long s_start[kBatchSmemSlots + 1];  // item offsets of the members, for the search
+  __shared__ long long s_start[kBatchSmemSlots + 1];  // cost offsets of the members
   const long long total = b.item_start[b.n];
+  const long long lo = total * (long long)blockIdx.x / gridDim.x;
+  const long long hi = total * (long long)(blockIdx.x + 1) / gridDim.x;
+  if (lo >= hi) return;
   const bool cached = b.n <= kBatchSmemSlots;
   if (cached)
     for (int i = threadIdx.x; i <= b.n; i += blockDim.x) s_start[i] = b.item_start[i];
@@ -1018,103 +1106,16 @@ __global__ void __launch_bounds__(512, MINB) k_batch_push(BatchDev b) {
   st.Es = reinterpret_cast<Real*>(smem_raw);
   st.Ss = reinterpret_cast<Acc*>(smem_raw + eb);
   st.Ls = reinterpret_cast<int*>(smem_raw + 2 * eb);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  while (true) {
-    if (threadIdx.x == 0) {
-      const long long item = (long long)atomicAdd(b.work_next, 1ull);
-      s_item = item;
-      if (item < total) {
-        int lo = 0, hi = b.n;  // last slot with item_start <= item
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (starts[mid] <= item) lo = mid;
-          else hi = mid;
-        }
-        s_slot = lo;
-      }
-    }
-    __syncthreads();
-    const long long item = s_item;
-    if (item >= total) break;
-    const int slot = s_slot;
-    {
-      const long long* src = reinterpret_cast<const long long*>(b.devs + slot);
-      long long* dst = reinterpret_cast<long long*>(&sd);
-      for (int w = threadIdx.x; w < (int)(sizeof(Dev) / 8); w += blockDim.x) dst[w] = src[w];
-    }
-    __syncthreads();
-    const Dev& d = sd;
-    Ctl* ctl = d.ctl;
-    const long long cc = ctl->conv_count;
-    const long long N0 = ctl->n[0] + cc, N1 = ctl->n[1] + cc;
-    const long long P = d.item_size;
-    const long long items0 = (N0 + P - 1) / P;
-    const long long local = item - starts[slot];
-    const int s = local < items0 ? 0 : 1;
-    const long long idx = s ? local - items0 : local;
-    const long long Ns = s ? N1 : N0;
-    const long long p0 = idx * P;
-    const long long p1 = min(p0 + P, Ns);
-    const long long c0 = p0 >> 2, c1 = (p1 + 3) >> 2;  // 4-particle chunks
-
-    const int nx = d.nx;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      st.Es[i] = (Real)d.E[i];
-      st.Ss[i] = Acc(0);
-      if (DEP == 4) st.Ls[i] = 0;
-    }
-    st.ctl = ctl;
-    st.ph_tail = ctl->ph_tail;
-    st.room = d.ph_cap - (st.ph_tail - ctl->conv_end);
-    st.ph_mask = d.ph_cap - 1;
-    set_scales<Real, DEP>(st, (double)(p1 - p0), d.dtdx);
-    __syncthreads();
-
-    double gsum = 0.0;
-    const long long nchunks = c1 - c0;
-    const long long iters = (nchunks + blockDim.x - 1) / blockDim.x;
-    const int pf = b.prefetch;
-    for (long long it = 0; it < iters; ++it) {
-      if (pf > 0 && lane == 0) {
-        // the warp's particles pf iterations ahead, inside this item
-        const long long chp = c0 + (it + pf) * blockDim.x + warp * 32;
-        if (chp < c1) {
-          const long long bp = chp * 4;
-          long long np = p1 - bp;
-          if (np > 128) np = 128;
-          if (np > 0) {
-            prefetch_l2(d.cell[s] + bp, (unsigned)(np * 4) & ~15u);
-            prefetch_l2(static_cast<const Real*>(d.off[s]) + bp, (unsigned)(np * sizeof(Real)) & ~15u);
-            prefetch_l2(static_cast<const Real*>(d.u[s]) + bp, (unsigned)(np * sizeof(Real)) & ~15u);
-          }
-        }
-      }
-      const long long ch = c0 + it * blockDim.x + warp * 32 + lane;
-      long long base = 0;
-      int cnt = 0;
-      if (ch < c1) {
-        base = ch * 4;
-        cnt = (int)min(4LL, p1 - base);
-      }
-      gsum += (double)process4<Real, kSmemESmemS, DEP, true, false>(d, st, s, base, cnt, lane);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) gsum += __shfl_down_sync(kFull, gsum, o);
-    if (lane == 0) red[warp] = gsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double v = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
-      atomicAdd(d.uk_part, v);
-    }
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      double v;
-      if (DEP == 1) v = (double)st.Ss[i] * (double)st.fx_inv;
-      else if (DEP == 4) v = (double)st.Ss[i] * (double)st.fx_inv + (double)st.Ls[i] * (double)st.lo_inv;
-      else v = (double)st.Ss[i];
-      if (v != 0.0) atomicAdd(d.S_glob + i, v);
-    }
-    __syncthreads();
+  int m = 0, top = b.n;  // last slot with starts[m] <= lo
+  while (top - m > 1) {
+    const int mid = (m + top) >> 1;
+    if (starts[mid] <= lo) m = mid;
+    else top = mid;
+  }
+  for (; m < b.n && starts[m] < hi; ++m) {
+    const long long s0 = starts[m], s1 = starts[m + 1];
+    if (s1 <= s0 || s1 <= lo) continue;  // idle member, or one that ends before this range
+    batch_range<Real, DEP>(b, sd, st, red, m, (lo > s0 ? lo : s0) - s0, (hi < s1 ? hi : s1) - s0);
   }
 }
 

@@ -26,8 +26,9 @@ def members_fp64():
 
 def test_batch_fp64_members_match_oracle():
     """Every member of an FP64 batch against the oracle, per step, to the
-    parity horizon (the batch adds each work item's current with FP64 atomics,
-    so only the summation order differs from the oracle)."""
+    parity horizon (the batch adds each CTA's current with FP64 atomics, so
+    only the summation order differs from the oracle).  These small members
+    are split across many CTAs by the cost-balanced partition."""
     ps = members_fp64()
     steps = 300
     with CascadeBatch(ps) as b:
