@@ -280,6 +280,7 @@ def main():
     assert len(rec["step"]) == args.steps
     ps = float((rec["n_elec"] + rec["n_posi"]).sum())
     n_now = int(rec["n_elec"][-1] + rec["n_posi"][-1])
+    pairs_timed = int(rec["n_pairs_total"][-1] - rec["n_pairs_total"][0])
 
     t_max, ps_all = aggregate_over_ranks(ms, ps, "cuda")
     value = ps_all / (t_max / 1e3)
@@ -322,6 +323,7 @@ def main():
                                    f"E0=100, gamma_thr=50, eps_gamma=20, l_pp=0.5, steps {args.prep + args.warmup}-"
                                    f"{args.prep + args.warmup + args.steps} (post-screening)",
                        "particles_per_step": ps / args.steps, "particles_at_end": n_now,
+                       "pairs_created_per_particle_step": pairs_timed / ps,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (particle state >> 129 MB)"},
             "roofline": roof,

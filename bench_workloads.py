@@ -70,11 +70,16 @@ def run_batch(args) -> int:
     ms = ev0.elapsed_time(ev1)
     ps = 0.0
     over = 0
+    pairs = photons = 0
     for i in range(len(scan)):
         try:
-            ps += _psteps(b.diag(i, args.batch_steps))
+            d = b.diag(i, args.batch_steps)
         except Exception:
             over += 1
+            continue
+        ps += _psteps(d)
+        pairs += int(d["n_pairs_total"][-1])
+        photons += int(d["n_pairs_total"][-1] + d["n_photon"][-1])
     b.close()
     value = ps / (ms / 1e3)
     fp64 = _fp64_one_at_a_time(scan[: args.fp64_sample], lambda p: args.batch_steps)
@@ -85,7 +90,9 @@ def run_batch(args) -> int:
         "config": {"workload": f"batched parameter scan: {len(scan)} cascades (Nx log-U[256,8192], ppc in "
                                "{8,16,32,64}, E0 and gamma_thr log-U[10,1000], eps = gamma_thr/2, l_pp U[0.2,2]), "
                                f"{args.batch_steps} steps each, {prec}, one launch per kernel per step",
-                   "members_over_capacity": over, "create_s": t_create, "wall_s": wall},
+                   "members_over_capacity": over, "create_s": t_create, "wall_s": wall,
+                   "pairs_created_per_particle_step": pairs / ps if ps else None,
+                   "photons_emitted_per_particle_step": photons / ps if ps else None},
         "fp64_one_at_a_time": dict(fp64, per_request_s=None,
                                    sample=f"first {args.fp64_sample} cascades of the scan, each alone in FP64"),
         "batched_over_fp64_one_at_a_time": value / fp64["value"] if fp64["value"] else None,

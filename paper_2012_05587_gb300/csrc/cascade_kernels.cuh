@@ -1085,12 +1085,34 @@ __device__ __forceinline__ void batch_range(const BatchDev& b, Dev& sd, PushStat
 // member only at member boundaries, so each CTA stages a member's E and
 // flushes its current once per launch, and its particles stream through in
 // order (prefetched into L2 ahead of use).
-template <class Real, int DEP, int MINB>
-__global__ void __launch_bounds__(512, MINB) k_batch_push(BatchDev b) {
+// Launch shapes of the batched particle kernel: threads per CTA and the CTAs
+// per SM its register budget is sized for (65536 registers per SM).  Shape 3
+// is the default (see batch_configure).
+template <int SHAPE>
+struct BatchShape;
+template <>
+struct BatchShape<0> {  // 2 x 512 threads, 64 registers
+  static constexpr int threads = 512, minb = 2;
+};
+template <>
+struct BatchShape<1> {  // 1 x 512 threads, up to 128 registers
+  static constexpr int threads = 512, minb = 1;
+};
+template <>
+struct BatchShape<2> {  // 1 x 768 threads, up to 80 registers
+  static constexpr int threads = 768, minb = 1;
+};
+template <>
+struct BatchShape<3> {  // 1 x 640 threads, up to 96 registers
+  static constexpr int threads = 640, minb = 1;
+};
+
+template <class Real, int DEP, int SHAPE>
+__global__ void __launch_bounds__(BatchShape<SHAPE>::threads, BatchShape<SHAPE>::minb) k_batch_push(BatchDev b) {
   typedef typename AccOf<Real, DEP>::type Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) Dev sd;
-  __shared__ double red[16];
+  __shared__ double red[32];
   __shared__ long long s_start[kBatchSmemSlots + 1];  // cost offsets of the members
   const long long total = b.item_start[b.n];
   const long long lo = total * (long long)blockIdx.x / gridDim.x;
@@ -1388,18 +1410,31 @@ struct Launchers {
     return cudaGetLastError();
   }
 
-  // minb: CTAs per SM the register budget is sized for (1: up to 128
-  // registers, no spills; 2: 64 registers)
-  static const void* batch_push_fn(int dep, int minb) {
+  template <int DEP>
+  static const void* batch_push_shape(int shape) {
+    switch (shape) {
+      case 1: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 1>);
+      case 2: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 2>);
+      case 3: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 3>);
+      default: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 0>);
+    }
+  }
+
+  // shape: see BatchShape
+  static const void* batch_push_fn(int dep, int shape) {
     if constexpr (sizeof(Real) == 8) {
-      return minb == 2 ? reinterpret_cast<const void*>(&k_batch_push<Real, 0, 2>)
-                       : reinterpret_cast<const void*>(&k_batch_push<Real, 0, 1>);
+      return batch_push_shape<0>(shape);
     } else {
-      if (dep == 4)
-        return minb == 2 ? reinterpret_cast<const void*>(&k_batch_push<Real, 4, 2>)
-                         : reinterpret_cast<const void*>(&k_batch_push<Real, 4, 1>);
-      return minb == 2 ? reinterpret_cast<const void*>(&k_batch_push<Real, 1, 2>)
-                       : reinterpret_cast<const void*>(&k_batch_push<Real, 1, 1>);
+      return dep == 4 ? batch_push_shape<4>(shape) : batch_push_shape<1>(shape);
+    }
+  }
+
+  static int batch_threads(int shape) {
+    switch (shape) {
+      case 1: return BatchShape<1>::threads;
+      case 2: return BatchShape<2>::threads;
+      case 3: return BatchShape<3>::threads;
+      default: return BatchShape<0>::threads;
     }
   }
 
@@ -1410,17 +1445,22 @@ struct Launchers {
     if (smem_bytes(max_nx, kSmemESmemS, dp) > limit && dp == 4) dp = 1;
     const size_t sm = smem_bytes(max_nx, kSmemESmemS, dp);
     if (sm > limit) return cudaErrorInvalidValue;
-    const int minb = env_int("CASCADE_BATCH_MINB", 2) == 1 ? 1 : 2;  // 2: measured faster
-    const void* fn = batch_push_fn(dp, minb);
+    // measured on the 256-cascade scan (3000 steps, FP32): shape 0 1.73e11,
+    // 1 1.69e11, 2 1.82e11, 3 1.87e11 particle-steps/s; the kernel keeps its
+    // member's descriptor in registers, so 64 registers spill
+    int shape = env_int("CASCADE_BATCH_SHAPE", 3);  // measurement override
+    if (shape < 0 || shape > 3) shape = 3;
+    const void* fn = batch_push_fn(dp, shape);
+    const int threads = batch_threads(shape);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, sm);
     if (e != cudaSuccess) return e;
     *grid = (per_sm < 1 ? 1 : per_sm) * num_sms;
-    *block = 512;
+    *block = threads;
     *smem = sm;
-    *dep = dp + 16 * minb;  // kernel selector: accumulator form and register budget
+    *dep = dp + 16 * shape;  // kernel selector: accumulator form and launch shape
     return cudaSuccess;
   }
 
