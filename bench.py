@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--save-series", default="", help="paper/corotating workloads: directory for the series")
     ap.add_argument("--corot-time", type=float, default=200.0, help="corotating workload: simulated time")
     ap.add_argument("--sweep-seeds", type=int, default=8, help="sweep workload: seeds averaged per configuration")
+    ap.add_argument("--sweep-rows", default="", help="sweep workload: comma-separated configuration indices (all)")
     return ap.parse_args()
 
 
@@ -133,6 +134,29 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def host_cpu() -> str:
+    """The host processor as /proc/cpuinfo names it (model name on x86; the
+    implementer and part codes on Arm), with the architecture and core count."""
+    import platform
+
+    model = None
+    fields = {}
+    try:
+        for line in open("/proc/cpuinfo"):
+            if ":" not in line:
+                continue
+            k, v = (x.strip() for x in line.split(":", 1))
+            if k == "model name" and model is None:
+                model = v
+            if k in ("CPU implementer", "CPU part") and k not in fields:
+                fields[k] = v
+    except OSError:
+        pass
+    if model is None and fields:
+        model = ", ".join(f"{k} {v}" for k, v in fields.items())
+    return f"{platform.machine()}, {os.cpu_count()} cores, {model or 'unknown model'}"
 
 
 def oracle_slice(steps_prep: int, steps_timed: int, multicore: bool = False):
@@ -213,7 +237,8 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": "large cascade slice Nx=512 (64+64 per cell, E0=100, gamma_thr=50, eps=20, "
                                "l_pp=0.5, dt=0.025, dx=0.05)", "l2": "state fits in host caches; CPU run"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -305,10 +330,11 @@ def main():
     cpu = cpu_mc = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, psx, el, nt, sample = oracle_slice(150, 60)
-        cpu = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": sample, "host": host_cpu()}
         try:
             v, psx, el, nt, sample = oracle_slice(150, 60, multicore=True)
-            cpu_mc = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle (OpenMP build)", "sample": sample}
+            cpu_mc = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle (OpenMP build)", "sample": sample,
+                      "host": host_cpu()}
         except Exception as e:  # no OpenMP runtime on the host
             cpu_mc = {"unavailable": str(e).splitlines()[0]}
 

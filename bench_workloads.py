@@ -181,18 +181,24 @@ def run_serve(args) -> int:
 def run_sweep(args) -> int:
     """Precision sweep: for each (E0, gamma_thr) the ensemble diagnostics of
     FP32-mixed and FP32-mixed-fine runs, averaged over seeds, against the same
-    average of all-FP64 runs (relative errors per diagnostic)."""
+    average of all-FP64 runs (relative errors per diagnostic).  A configuration
+    whose predicted particle count exceeds the capacity runs one seed only, to
+    show the capacity error it returns."""
     from paper_2012_05587_gb300 import Cascade, CascadeError, analysis, workloads as W
 
     rows = []
-    seeds = list(range(args.sweep_seeds))
-    for idx in range(9):
+    n_cfg = len(W.precision_sweep(run=0))
+    which = [int(x) for x in args.sweep_rows.split(",")] if args.sweep_rows else list(range(n_cfg))
+    for idx in which:
+        t_row = time.perf_counter()
+        p0 = W.precision_sweep(run=0)[idx]
+        predicted = W.predicted_particles(p0)
+        over = predicted > 2 * p0["particle_cap"]
+        seeds = [0] if over else list(range(args.sweep_seeds))
         res = {"fp64": [], "fp32": [], "fp32_fine": []}
         errs = {}
-        p0 = None
         for run in seeds:
             p = W.precision_sweep(run=run)[idx]
-            p0 = p
             for prec in res:
                 q = dict(p, precision=prec)
                 if prec == "fp64":
@@ -204,7 +210,8 @@ def run_sweep(args) -> int:
                     res[prec].append(analysis.ensemble(rec))
                 except CascadeError as e:
                     errs[prec] = str(e).split(":")[1].strip() if ":" in str(e) else str(e)
-        row = {"E0": p0["E0"], "gamma_thr": p0["gamma_thr"], "dt": p0["dt"], "seeds": len(seeds)}
+        row = {"E0": p0["E0"], "gamma_thr": p0["gamma_thr"], "dt": p0["dt"], "seeds": len(seeds),
+               "predicted_particles": predicted}
         if errs:
             row["errors"] = errs
         else:
@@ -212,6 +219,7 @@ def run_sweep(args) -> int:
             row["fp64_mean"] = mean["fp64"]
             row["fp32_rel_err"] = analysis.relative_errors(mean["fp32"], mean["fp64"])
             row["fp32_fine_rel_err"] = analysis.relative_errors(mean["fp32_fine"], mean["fp64"])
+        row["seconds"] = time.perf_counter() - t_row
         rows.append(row)
         print(json.dumps({"sweep_row": row}), flush=True)
     line = {"metric": B.METRIC, "value": None, "unit": UNIT, "workload": "precision sweep", "rows": rows}

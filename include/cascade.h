@@ -197,9 +197,10 @@ int cascade_timing(cascade_t* h, double* particle_kernel_ms, int64_t* particle_k
 /* ---------------------------------------------------------------------------
  * Batches: many independent cascades (uneven grids and particle counts)
  * advanced together.  One step is four launches for the whole batch: photon
- * conversion of every member, a plan that cuts every member's particles into
- * work items, one persistent particle kernel that hands the items out
- * dynamically, and one field kernel with a CTA per member.  Steps are
+ * conversion of every member, a plan that prices every member's particles
+ * (plus a fixed share per member), one persistent particle kernel whose CTAs
+ * each take an equal contiguous part of that cost, and one field kernel with
+ * a CTA per member.  Steps are
  * replayed from a captured CUDA graph.  Each member keeps its own step
  * target; members that reach it stop.  All members share the batch's
  * precision (CASCADE_FP64 or one of the FP32 modes) and nx <= max_nx.

@@ -68,6 +68,7 @@ struct Dev {
   int variant;         // particle-kernel variant, see PushVariant
   int push_dep;        // current accumulator, see AccOf in cascade_kernels.cuh
   int push_fast;       // 1: gamma from one reciprocal square root (FP32 only)
+  int push_stage;      // 1: particles staged through shared memory with cp.async (FP32)
   int fine_deposit;    // FP32: two-word accumulator (CASCADE_FP32_MIXED_FINE)
   int prefetch;        // particle kernel: iterations ahead to prefetch into L2 (0 = off)
   int open_bc;         // 1: open boundaries (co-rotating frame runs), 0: periodic

@@ -24,7 +24,7 @@ namespace cpic {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kFieldGroups = 8;  // row groups of the field kernel (kFieldBlock / 32)
-constexpr int kBatchSmemSlots = 1024;  // batches up to this size keep the item offsets in shared memory
+constexpr int kBatchSmemSlots = 1024;  // batches up to this size keep the cost offsets in shared memory
 // Upper bound on photons one lepton emits in one step (a step that needs more
 // is far too coarse for the model; the count is clamped).
 constexpr int kMaxPhotonsPerStep = 1 << 16;
@@ -59,6 +59,17 @@ __device__ __forceinline__ void set_error(Ctl* ctl, int code) { atomicCAS(&ctl->
 __device__ __forceinline__ void prefetch_l2(const void* ptr, unsigned bytes) {
   if (bytes >= 16) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
 }
+
+// Asynchronous copy of one 16-byte chunk into shared memory (both addresses
+// 16-byte aligned); only the first `bytes` are read, the rest is zero-filled.
+// The issuing thread waits for its own copies with cp.async.wait_group, a
+// hardware wait that ends when the copies land (no spin loop).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, unsigned bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Seed: quiet start, pair j in cell j mod nx at offset (j div nx + 1/2)/ppc,
@@ -265,9 +276,12 @@ __device__ __forceinline__ void set_scales(PushState<Real, DEP>& st, double pcou
 // edges, a particle crossing x = 0 or x = L deposits the part of its path
 // inside and is marked departed (cell -1, index appended to the hole list),
 // a photon whose conversion point lies outside is not kept.
-template <class Real, int V, int DEP, bool FAST, bool OPEN>
+// STG: the four particles were already copied into this thread's shared
+// memory slots stg[0..2] (cell, offset, momentum; zero beyond cnt) by
+// cp.async; otherwise they are loaded from global memory here.
+template <class Real, int V, int DEP, bool FAST, bool OPEN, bool STG = false>
 __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP>& st, int s, long long base,
-                                         int cnt, int lane) {
+                                         int cnt, int lane, const unsigned char* const* stg = nullptr) {
   typedef typename AccOf<Real, DEP>::type Acc;
   const int nx = d.nx;
   const Real dt = (Real)d.dt, dtdx = (Real)d.dtdx;
@@ -278,7 +292,13 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
   Real* up = static_cast<Real*>(d.u[s]) + base;
   int cl[4] = {0, 0, 0, 0};
   Real of[4] = {zero, zero, zero, zero}, uu[4] = {zero, zero, zero, zero};
-  if (cnt == 4) {
+  if (STG) {
+    if (cnt > 0) {
+      ld4(reinterpret_cast<const int*>(stg[0]), cl);
+      ld4(reinterpret_cast<const Real*>(stg[1]), of);
+      ld4(reinterpret_cast<const Real*>(stg[2]), uu);
+    }
+  } else if (cnt == 4) {
     ld4(cellp, cl);
     ld4(offp, of);
     ld4(up, uu);
@@ -589,8 +609,26 @@ struct PushBlock {
   static constexpr int value = sizeof(Real) == 8 ? 512 : 1024;
 };
 
-template <class Real, int V, int DEP, bool FAST, bool OPEN>
+// Shared memory of the particle kernel for E and the current accumulator:
+// E (Real) plus one Real or int32 word per edge, two int32 words for DEP 4.
+template <class Real>
+__host__ __device__ inline size_t smem_field_bytes(int nx, int variant, int dep) {
+  const size_t eb = ((size_t)nx * sizeof(Real) + 15) & ~size_t(15);
+  if (variant == kSmemESmemS) return (dep == 4 ? 3 : 2) * eb;
+  if (variant == kSmemEGlobS || variant == kGlobESmemS) return eb;
+  return 0;
+}
+
+// Bytes of the cp.async staging area of the particle kernel: two stages of
+// three 16-byte slots (cell, offset, momentum of four particles) per thread.
+constexpr size_t kStageBytesPerThread = 2 * 3 * 16;
+
+// STG (FP32 only): the particles of the next iteration are copied into
+// shared memory with cp.async while the current ones are processed, so each
+// thread keeps one iteration of loads in flight at all times.
+template <class Real, int V, int DEP, bool FAST, bool OPEN, bool STG = false>
 __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
+  static_assert(!STG || sizeof(Real) == 4, "the staging slots hold four 4-byte values");
   typedef typename AccOf<Real, DEP>::type Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
@@ -629,6 +667,24 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  // this thread's staging slots: [stage][array][thread][16 B]
+  unsigned char* stage = smem_raw + smem_field_bytes<Real>(nx, V, DEP);
+  const size_t slab = (size_t)blockDim.x * 16;
+  auto slot = [&](int b, int a) { return stage + (size_t)(b * 3 + a) * slab + (size_t)threadIdx.x * 16; };
+  auto issue = [&](long long it) {  // cp.async of iteration it's chunk into stage it & 1
+    const long long ch = first_wb + it * stride + warp * 32 + lane;
+    if (it < iters_cta && ch < C) {
+      const int sp = ch < C0 ? 0 : 1;
+      const long long bp = (ch - (sp ? C0 : 0)) * 4;
+      const unsigned bytes = (unsigned)min(4LL, (sp ? N1 : N0) - bp) * 4u;
+      const int b = (int)(it & 1);
+      cp_async16(slot(b, 0), d.cell[sp] + bp, bytes);
+      cp_async16(slot(b, 1), static_cast<const Real*>(d.off[sp]) + bp, bytes);
+      cp_async16(slot(b, 2), static_cast<const Real*>(d.u[sp]) + bp, bytes);
+    }
+    cp_async_commit();  // one group per iteration, empty or not
+  };
+  if (STG) issue(0);
   double gsum_total = 0.0;
   const int pf = d.prefetch;  // iterations ahead that lane 0 prefetches its warp's particles
   for (long long it = 0; it < iters_cta; ++it) {
@@ -655,7 +711,15 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
       const long long N = s ? N1 : N0;
       cnt = (int)min(4LL, N - base);
     }
-    gsum_total += (double)process4<Real, V, DEP, FAST, OPEN>(d, st, s, base, cnt, lane);
+    if (STG) {
+      issue(it + 1);
+      cp_async_wait_prev();  // iteration it's copies have landed
+      const int b = (int)(it & 1);
+      const unsigned char* stg[3] = {slot(b, 0), slot(b, 1), slot(b, 2)};
+      gsum_total += (double)process4<Real, V, DEP, FAST, OPEN, true>(d, st, s, base, cnt, lane, stg);
+    } else {
+      gsum_total += (double)process4<Real, V, DEP, FAST, OPEN>(d, st, s, base, cnt, lane);
+    }
   }
 
   // sum of gamma over the CTA (FP64)
@@ -895,12 +959,13 @@ __global__ void k_compact_move(Dev d) {
 
 // ---------------------------------------------------------------------------
 // Batched cascades.  Per step: conversion for every member (one row of CTAs
-// per member), a one-CTA plan that cuts every member's particles into work
-// items, the persistent particle kernel that hands items out dynamically
-// (each item stages its own member's E and accumulates its current in shared
-// memory, then adds it to the member's FP64 current with global atomics),
-// and the field kernel (one CTA per member).  Members whose remaining step
-// count is zero are skipped by all four.
+// per member), a one-CTA plan that prices every member's particles and scans
+// the costs, the persistent particle kernel whose CTAs each take an equal
+// contiguous part of the total cost (staging each member's E and
+// accumulating its current in shared memory, then adding it to the member's
+// FP64 current with global atomics), and the field kernel (one CTA per
+// member).  Members whose remaining step count is zero are skipped by all
+// four.
 // ---------------------------------------------------------------------------
 template <class Real>
 __global__ void k_batch_convert(BatchDev b) {
@@ -998,9 +1063,9 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchDev b) {
 // 1's), clipped to the member's chunk count: copy its descriptor, stage its E
 // and clear the accumulator, advance the particles, then add the CTA's sum of
 // gamma and current to the member's FP64 totals with global atomics.
-template <class Real, int DEP>
+template <class Real, int DEP, bool STG>
 __device__ __forceinline__ void batch_range(const BatchDev& b, Dev& sd, PushState<Real, DEP>& st, double* red,
-                                            int slot, long long a, long long e) {
+                                            unsigned char* stage, int slot, long long a, long long e) {
   typedef typename AccOf<Real, DEP>::type Acc;
   {
     const long long* src = reinterpret_cast<const long long*>(b.devs + slot);
@@ -1035,6 +1100,23 @@ __device__ __forceinline__ void batch_range(const BatchDev& b, Dev& sd, PushStat
   double gsum = 0.0;
   const long long iters = (e - a + blockDim.x - 1) / blockDim.x;
   const int pf = b.prefetch;
+  // this thread's staging slots (STG): [stage][array][thread][16 B]
+  const size_t slab = (size_t)blockDim.x * 16;
+  auto slot_of = [&](int bb, int arr) { return stage + (size_t)(bb * 3 + arr) * slab + (size_t)threadIdx.x * 16; };
+  auto issue = [&](long long it) {  // cp.async of iteration it's chunk into stage it & 1
+    const long long ch = a + it * blockDim.x + warp * 32 + lane;
+    if (it < iters && ch < e) {
+      const int sp = ch < C0 ? 0 : 1;
+      const long long bp = (ch - (sp ? C0 : 0)) * 4;
+      const unsigned bytes = (unsigned)min(4LL, (sp ? N1 : N0) - bp) * 4u;
+      const int bb = (int)(it & 1);
+      cp_async16(slot_of(bb, 0), d.cell[sp] + bp, bytes);
+      cp_async16(slot_of(bb, 1), static_cast<const Real*>(d.off[sp]) + bp, bytes);
+      cp_async16(slot_of(bb, 2), static_cast<const Real*>(d.u[sp]) + bp, bytes);
+    }
+    cp_async_commit();  // one group per iteration, empty or not
+  };
+  if (STG) issue(0);
   for (long long it = 0; it < iters; ++it) {
     if (pf > 0 && lane == 0) {
       // the warp's particles pf iterations ahead, inside this range
@@ -1059,7 +1141,15 @@ __device__ __forceinline__ void batch_range(const BatchDev& b, Dev& sd, PushStat
       base = (ch - (s ? C0 : 0)) * 4;
       cnt = (int)min(4LL, (s ? N1 : N0) - base);
     }
-    gsum += (double)process4<Real, kSmemESmemS, DEP, true, false>(d, st, s, base, cnt, lane);
+    if (STG) {
+      issue(it + 1);
+      cp_async_wait_prev();  // iteration it's copies have landed
+      const int bb = (int)(it & 1);
+      const unsigned char* stg[3] = {slot_of(bb, 0), slot_of(bb, 1), slot_of(bb, 2)};
+      gsum += (double)process4<Real, kSmemESmemS, DEP, true, false, true>(d, st, s, base, cnt, lane, stg);
+    } else {
+      gsum += (double)process4<Real, kSmemESmemS, DEP, true, false>(d, st, s, base, cnt, lane);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) gsum += __shfl_down_sync(kFull, gsum, o);
@@ -1107,8 +1197,11 @@ struct BatchShape<3> {  // 1 x 640 threads, up to 96 registers
   static constexpr int threads = 640, minb = 1;
 };
 
-template <class Real, int DEP, int SHAPE>
+// STG (FP32): particles staged through shared memory with cp.async, as in
+// the single-cascade kernel; the staging area follows E and the accumulator.
+template <class Real, int DEP, int SHAPE, bool STG>
 __global__ void __launch_bounds__(BatchShape<SHAPE>::threads, BatchShape<SHAPE>::minb) k_batch_push(BatchDev b) {
+  static_assert(!STG || sizeof(Real) == 4, "the staging slots hold four 4-byte values");
   typedef typename AccOf<Real, DEP>::type Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) Dev sd;
@@ -1128,6 +1221,7 @@ __global__ void __launch_bounds__(BatchShape<SHAPE>::threads, BatchShape<SHAPE>:
   st.Es = reinterpret_cast<Real*>(smem_raw);
   st.Ss = reinterpret_cast<Acc*>(smem_raw + eb);
   st.Ls = reinterpret_cast<int*>(smem_raw + 2 * eb);
+  unsigned char* stage = smem_raw + (DEP == 4 ? 3 : 2) * eb;
   int m = 0, top = b.n;  // last slot with starts[m] <= lo
   while (top - m > 1) {
     const int mid = (m + top) >> 1;
@@ -1137,7 +1231,7 @@ __global__ void __launch_bounds__(BatchShape<SHAPE>::threads, BatchShape<SHAPE>:
   for (; m < b.n && starts[m] < hi; ++m) {
     const long long s0 = starts[m], s1 = starts[m + 1];
     if (s1 <= s0 || s1 <= lo) continue;  // idle member, or one that ends before this range
-    batch_range<Real, DEP>(b, sd, st, red, m, (lo > s0 ? lo : s0) - s0, (hi < s1 ? hi : s1) - s0);
+    batch_range<Real, DEP, STG>(b, sd, st, red, stage, m, (lo > s0 ? lo : s0) - s0, (hi < s1 ? hi : s1) - s0);
   }
 }
 
@@ -1276,10 +1370,10 @@ __global__ void k_gauss_reduce(Dev d, const double* rho_dx, double* out) {
 // accumulator.
 template <class Real>
 struct PushTable {
-  static const void* get(int V, int dep, bool fast, bool open);
+  static const void* get(int V, int dep, bool fast, bool open, bool stage);
 };
 template <>
-inline const void* PushTable<double>::get(int V, int, bool, bool open) {
+inline const void* PushTable<double>::get(int V, int, bool, bool open, bool) {
   if (V == kSmemESmemS)
     return open ? reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false, true>)
                 : reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false, false>);
@@ -1290,8 +1384,10 @@ inline const void* PushTable<double>::get(int V, int, bool, bool open) {
   return reinterpret_cast<const void*>(&k_push<double, kGlobEGlobS, 0, false, false>);
 }
 template <>
-inline const void* PushTable<float>::get(int V, int dep, bool, bool open) {
+inline const void* PushTable<float>::get(int V, int dep, bool, bool open, bool stage) {
   if (V == kSmemESmemS) {
+    if (stage && !open && dep == 1)
+      return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, false, true>);
     if (open) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, true>);
     if (dep == 4) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 4, true, false>);
     return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, false>);
@@ -1311,17 +1407,15 @@ inline int env_int(const char* name, int dflt) {
 
 template <class Real>
 struct Launchers {
-  // E (Real) plus the accumulator: one Real or int32 word per edge, two
-  // int32 words for DEP 4.
-  static size_t smem_bytes(int nx, int variant, int dep = 0) {
-    const size_t eb = ((size_t)nx * sizeof(Real) + 15) & ~size_t(15);
-    if (variant == kSmemESmemS) return (dep == 4 ? 3 : 2) * eb;
-    if (variant == kSmemEGlobS || variant == kGlobESmemS) return eb;
-    return 0;
+  static size_t smem_bytes(int nx, int variant, int dep = 0) { return smem_field_bytes<Real>(nx, variant, dep); }
+
+  // dynamic shared memory of one particle-kernel launch
+  static size_t push_smem(const Dev& d) {
+    return smem_bytes(d.nx, d.variant, d.push_dep) + (d.push_stage ? kStageBytesPerThread * d.block_push : 0);
   }
 
   static const void* push_fn(const Dev& d) {
-    return PushTable<Real>::get(d.variant, d.push_dep, d.push_fast != 0, d.open_bc != 0);
+    return PushTable<Real>::get(d.variant, d.push_dep, d.push_fast != 0, d.open_bc != 0, d.push_stage != 0);
   }
 
   static cudaError_t configure(Dev& d, int num_sms) {
@@ -1358,16 +1452,26 @@ struct Launchers {
     d.variant = variant;
     d.push_dep = dep;
     d.push_fast = fast;
-    const size_t smem = smem_bytes(d.nx, variant, dep);
+    const int block = PushBlock<Real>::value;
+    d.block_push = block;
+    d.push_stage = 0;
+    if (sizeof(Real) == 4 && variant == kSmemESmemS && dep == 1 && !d.open_bc &&
+        env_int("CASCADE_PUSH_STAGE", 1) == 1) {
+      // the staging area must fit beside E and the accumulator (1 KB left
+      // for the kernel's static shared memory)
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (smem_bytes(d.nx, variant, dep) + kStageBytesPerThread * block + 1024 <= (size_t)optin) d.push_stage = 1;
+    }
+    const size_t smem = push_smem(d);
     const void* fn = push_fn(d);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int block = PushBlock<Real>::value;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    d.block_push = block;
     d.grid_push = per_sm * num_sms;
     d.prefetch = env_int("CASCADE_PUSH_PREFETCH", 1);  // one iteration ahead: measured +4.6%
     if (d.prefetch < 0 || d.prefetch > 8) d.prefetch = 0;
@@ -1395,7 +1499,7 @@ struct Launchers {
     Dev arg = d;
     void* args[] = {&arg};
     cudaError_t e = cudaLaunchKernel(push_fn(d), dim3(d.grid_push), dim3(d.block_push), args,
-                                     smem_bytes(d.nx, d.variant, d.push_dep), st);
+                                     push_smem(d), st);
     if (e != cudaSuccess) return e;
     if (after) cudaEventRecord(after, st);
     if (d.open_bc) {
@@ -1410,24 +1514,27 @@ struct Launchers {
     return cudaGetLastError();
   }
 
-  template <int DEP>
+  template <int DEP, bool STG>
   static const void* batch_push_shape(int shape) {
     switch (shape) {
-      case 1: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 1>);
-      case 2: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 2>);
-      case 3: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 3>);
-      default: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 0>);
+      case 1: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 1, STG>);
+      case 2: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 2, STG>);
+      case 3: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 3, STG>);
+      default: return reinterpret_cast<const void*>(&k_batch_push<Real, DEP, 0, STG>);
     }
   }
 
-  // shape: see BatchShape
-  static const void* batch_push_fn(int dep, int shape) {
+  // shape: see BatchShape; stage: cp.async staging (FP32 only)
+  static const void* batch_push_fn(int dep, int shape, bool stage) {
     if constexpr (sizeof(Real) == 8) {
-      return batch_push_shape<0>(shape);
+      return batch_push_shape<0, false>(shape);
     } else {
-      return dep == 4 ? batch_push_shape<4>(shape) : batch_push_shape<1>(shape);
+      if (stage) return dep == 4 ? batch_push_shape<4, true>(shape) : batch_push_shape<1, true>(shape);
+      return dep == 4 ? batch_push_shape<4, false>(shape) : batch_push_shape<1, false>(shape);
     }
   }
+
+  static int BatchShapeMinb(int shape) { return shape == 0 ? BatchShape<0>::minb : 1; }
 
   static int batch_threads(int shape) {
     switch (shape) {
@@ -1450,17 +1557,29 @@ struct Launchers {
     // member's descriptor in registers, so 64 registers spill
     int shape = env_int("CASCADE_BATCH_SHAPE", 3);  // measurement override
     if (shape < 0 || shape > 3) shape = 3;
-    const void* fn = batch_push_fn(dp, shape);
     const int threads = batch_threads(shape);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // FP32: stage the particles through shared memory where the staging area
+    // fits beside E and the accumulator (1 KB left for static shared memory)
+    int stage = 0;
+    if (sizeof(Real) == 4 && env_int("CASCADE_BATCH_STAGE", 1) == 1) {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      const size_t need = (sm + kStageBytesPerThread * threads) * BatchShapeMinb(shape) + 1024;
+      if (need <= (size_t)optin) stage = 1;
+    }
+    const size_t smem_total = sm + (stage ? kStageBytesPerThread * threads : 0);
+    const void* fn = batch_push_fn(dp, shape, stage != 0);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_total);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem_total);
     if (e != cudaSuccess) return e;
     *grid = (per_sm < 1 ? 1 : per_sm) * num_sms;
     *block = threads;
-    *smem = sm;
-    *dep = dp + 16 * shape;  // kernel selector: accumulator form and launch shape
+    *smem = smem_total;
+    // kernel selector: accumulator form, launch shape, staging
+    *dep = dp + 16 * shape + 64 * stage;
     return cudaSuccess;
   }
 
@@ -1469,7 +1588,8 @@ struct Launchers {
     k_batch_plan<Real><<<1, 1024, 0, st>>>(b);
     BatchDev arg = b;
     void* args[] = {&arg};
-    cudaError_t e = cudaLaunchKernel(batch_push_fn(dep % 16, dep / 16), dim3(grid), dim3(block), args, smem, st);
+    cudaError_t e = cudaLaunchKernel(batch_push_fn(dep % 16, (dep / 16) % 4, dep / 64 != 0), dim3(grid), dim3(block),
+                                     args, smem, st);
     if (e != cudaSuccess) return e;
     k_batch_field<Real><<<b.n, kFieldBlock, 0, st>>>(b);
     return cudaGetLastError();

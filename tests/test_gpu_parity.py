@@ -235,6 +235,31 @@ def test_large_cascade_first_steps(precision, tol):
             np.testing.assert_allclose(g["u"][idx], pr["u"][2 * idx + s], rtol=tol, atol=tol)
 
 
+def test_staged_particle_stream_matches_direct_loads(monkeypatch):
+    """The FP32 particle kernel reads its particles either through cp.async
+    staging in shared memory (the default where it fits) or with direct loads.
+    Without emission (gamma_thr out of reach) both give bit-identical fields
+    and particles; 2 x 1,032,129 particles on Nx = 16383 span several
+    iterations per CTA and end in a ragged chunk."""
+    p = dict(W.large_cascade(precision="fp32"), nx=16383, ppc=63, gamma_thr=1e9, eps_gamma=20.0,
+             particle_cap=1 << 21, u_spread=0.3)
+    out = {}
+    for stage in ("1", "0"):
+        monkeypatch.setenv("CASCADE_PUSH_STAGE", stage)
+        with Cascade(p) as c:
+            c.step(50)
+            d = c.diag(50)
+            out[stage] = (c.fields(), c.particles(0), c.particles(1), d)
+    (E1, J1), a1, b1, d1 = out["1"]
+    (E0, J0), a0, b0, d0 = out["0"]
+    assert np.abs(d1["E_absmax"]).max() > 0
+    assert np.array_equal(E1, E0) and np.array_equal(J1, J0)
+    for x, y in ((a1, a0), (b1, b0)):
+        for k in ("cell", "off", "u"):
+            assert np.array_equal(x[k], y[k]), k
+    assert np.array_equal(d1["E_mean"], d0["E_mean"]) and np.array_equal(d1["U_K"], d0["U_K"])
+
+
 # --- errors ------------------------------------------------------------------------------------
 
 def test_capacity_overflow_is_reported():
