@@ -38,9 +38,10 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s incl. deposit+QED (batched FP32 vs plain FP64), % HBM roofline; p50/p99"
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = {"fp32": 24, "fp64": 40}
-# DRAM bytes (read + write) per particle-step of the FP32 particle kernel, from
-# one ncu capture of this kernel on a smaller post-screening case of the same
-# grid (profiles/k_push_fp32_post_screening.md: 785.0 MB for 3.487e7
+# DRAM bytes (read + write) per particle-step of the FP32 particle kernel (the
+# form that stages its particles through shared memory), from one ncu capture
+# of this kernel on a smaller post-screening case of the same grid
+# (profiles/k_push_fp32_post_screening.md: 785.3 MB for 3.487e7
 # particle-steps); traffic grows in proportion to the particles processed.
 MEASURED_DRAM_BYTES_PER_PARTICLE_STEP = {"fp32": 22.52}
 
