@@ -44,6 +44,15 @@ BYTES_PER_PARTICLE_STEP = {"fp32": 24, "fp64": 40}
 # (profiles/k_push_fp32_post_screening.md: 785.3 MB for 3.487e7
 # particle-steps); traffic grows in proportion to the particles processed.
 MEASURED_DRAM_BYTES_PER_PARTICLE_STEP = {"fp32": 22.52}
+# The FP64 particle kernel is bound by the FP64 pipe, not by HBM: ncu counted
+# 45,085,174 FP64-pipe warp instructions for 34,865,152 particle-steps
+# (sm__inst_executed_pipe_fp64.sum on the same post-screening case as above,
+# with the FP64 pipe busy 84.9% of the cycles and DRAM at 6%).  The pipe's peak is
+# 9.5 warp instructions per cycle for the GPU: one per 16 cycles on each of
+# the 152 SMs (2 FP64 lanes per SM per cycle, which is 1.26 TFLOP/s of FMA at
+# 2.07 GHz); ncu reports the same figure as the metric's peak_sustained.
+FP64_PIPE_INST_PER_PARTICLE_STEP = 45_085_174 / 34_865_152
+FP64_PIPE_PEAK_INST_PER_CYCLE = 152 / 16
 
 
 def parse():
@@ -321,6 +330,18 @@ def main():
             "traffic": traffic, "traffic_source": "ncu capture of a smaller case scaled per particle-step"
             if tb else None, "kernel": "k_push (gather/push/move/deposit/emission)",
             "bytes_per_particle_step": bpp, "peak_source": peak_kind}
+    if prec == "fp64":
+        # FP64-pipe bound: warp instructions per second against the pipe's
+        # peak at the SM clock sampled during the timed region
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        a = FP64_PIPE_INST_PER_PARTICLE_STEP * ps / args.steps / avg_push_s / 1e9
+        pk = FP64_PIPE_PEAK_INST_PER_CYCLE * mhz * 1e6 / 1e9
+        roof = {"bound": "alu", "achieved": a, "peak": pk, "unit": "G FP64 warp-inst/s", "frac": a / pk,
+                "traffic": None, "kernel": "k_push (gather/push/move/deposit/emission), FP64",
+                "inst_per_particle_step": FP64_PIPE_INST_PER_PARTICLE_STEP,
+                "peak_source": "152 SMs x 1 FP64 warp instruction per 16 cycles x sampled SM clock",
+                "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "bytes_per_particle_step": bpp}}
 
     # end to end through the C ABI with host buffers
     e2e = None
