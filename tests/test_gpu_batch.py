@@ -133,3 +133,32 @@ def test_served_request_matches_running_alone():
     assert hz > 100
     m = d_alone["step"] < hz
     assert np.abs(d_mix["E_mean"][m] - d_alone["E_mean"][m]).max() <= T.RTOL * np.abs(d_alone["E_absmax"]).max()
+
+
+def test_full_scan_members_match_oracle_first_steps():
+    """The benchmark's launch configuration: all 256 cascades of the seeded
+    parameter scan in one FP32 batch.  For the first 60 steps, five members
+    (the three smallest, the median and the largest) are compared with the
+    FP64 oracle running each alone: E and J per edge to 2e-4 of max |E|, and
+    the counts within 1%."""
+    scan = [dict(q) for q in W.batch_scan(256)]
+    for q in scan:
+        q.pop("steps")
+    steps = 60
+    order = sorted(range(len(scan)), key=lambda i: scan[i]["nx"] * scan[i]["ppc"])
+    picks = order[:3] + [order[len(order) // 2], order[-1]]
+    with CascadeBatch(scan) as b:
+        b.step([steps] * len(scan))
+        for i in picks:
+            p = scan[i]
+            d = b.diag(i, steps)
+            E, J = b.fields(i)
+            ref = oracle.Oracle(T.oracle_params(p))
+            d_ref = ref.step(steps)
+            E_ref, J_ref = ref.fields()
+            scale = np.abs(E_ref).max()
+            assert np.abs(E - E_ref).max() <= 2e-4 * scale, i
+            assert np.abs(J - J_ref).max() <= 2e-3 * max(np.abs(J_ref).max(), 1e-12) + 2e-4 * scale, i
+            for k in ("n_elec", "n_posi", "n_pairs_total"):
+                assert abs(d[k][-1] - d_ref[k][-1]) <= 0.01 * max(d_ref[k][-1], 1), (i, k)
+            assert np.allclose(d["E_mean"], d_ref["E_mean"], rtol=0, atol=2e-4 * scale), i
