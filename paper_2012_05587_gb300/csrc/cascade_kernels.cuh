@@ -1536,7 +1536,7 @@ struct Launchers {
     }
   }
 
-  static int BatchShapeMinb(int shape) { return shape == 0 ? BatchShape<0>::minb : 1; }
+  static int batch_minb(int shape) { return shape == 0 ? BatchShape<0>::minb : 1; }
 
   static int batch_threads(int shape) {
     switch (shape) {
@@ -1567,7 +1567,7 @@ struct Launchers {
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      const size_t need = (sm + kStageBytesPerThread * threads) * BatchShapeMinb(shape) + 1024;
+      const size_t need = (sm + kStageBytesPerThread * threads) * batch_minb(shape) + 1024;
       if (need <= (size_t)optin) stage = 1;
     }
     const size_t smem_total = sm + (stage ? kStageBytesPerThread * threads : 0);
