@@ -162,3 +162,26 @@ def test_full_scan_members_match_oracle_first_steps():
             for k in ("n_elec", "n_posi", "n_pairs_total"):
                 assert abs(d[k][-1] - d_ref[k][-1]) <= 0.01 * max(d_ref[k][-1], 1), (i, k)
             assert np.allclose(d["E_mean"], d_ref["E_mean"], rtol=0, atol=2e-4 * scale), i
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_fine"])
+def test_fp32_batch_members_match_oracle_first_steps(precision):
+    """Both FP32 accumulator forms of the batched particle kernel (one int32
+    word per edge, and the two-word fine form) against the FP64 oracle: the
+    uneven members of the FP64 test, 80 steps (through the first emissions
+    and conversions), E per edge and the per-step mean field to 5e-4 of
+    max |E|, pair counts within 2%."""
+    ps = [dict(p, precision=precision) for p in members_fp64()]
+    steps = 80
+    with CascadeBatch(ps) as b:
+        b.step([steps] * len(ps))
+        for i, p in enumerate(ps):
+            d = b.diag(i, steps)
+            E, _ = b.fields(i)
+            ref = oracle.Oracle(T.oracle_params(p))
+            d_ref = ref.step(steps)
+            E_ref, _ = ref.fields()
+            scale = np.abs(d_ref["E_absmax"]).max()
+            assert np.abs(E - E_ref).max() <= 5e-4 * scale, i
+            assert np.abs(d["E_mean"] - d_ref["E_mean"]).max() <= 5e-4 * scale, i
+            assert abs(d["n_pairs_total"][-1] - d_ref["n_pairs_total"][-1]) <= 0.02 * max(d_ref["n_pairs_total"][-1], 1)
