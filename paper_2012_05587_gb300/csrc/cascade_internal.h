@@ -24,7 +24,7 @@ struct Ctl {
   int err;                        // first device-side error (cascade_status), 0 if none
   int active_blocks;              // particle-kernel CTAs that work in the current step
   unsigned int field_ticket;      // last-block detection in the field kernel
-  int pad_;
+  float part_inv;                 // FP32 int32 current partials: the common scale 2^-k
   // open boundaries: departed particles of the current step and the
   // compaction that fills their slots
   unsigned long long n_holes[2];  // departed (hole-list entries, may exceed the list)

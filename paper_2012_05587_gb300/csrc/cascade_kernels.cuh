@@ -14,6 +14,7 @@
 //              and writes the per-step record
 #pragma once
 
+#include <type_traits>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -663,7 +664,11 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
   const long long stride = (long long)G * blockDim.x;
   const long long first_wb = (long long)blockIdx.x * blockDim.x;
   const long long iters_cta = (C > first_wb) ? (C - first_wb + stride - 1) / stride : 0;
-  set_scales<Real, DEP>(st, (double)(iters_cta * blockDim.x * 4), d.dtdx);
+  // every CTA takes the scale of the busiest one (CTA 0), so the int32 rows
+  // of DEP 1 share one scale and the field kernel sums them exactly
+  const long long iters_max = (C + stride - 1) / stride;
+  set_scales<Real, DEP>(st, (double)(iters_max * blockDim.x * 4), d.dtdx);
+  if (DEP == 1 && blockIdx.x == 0 && threadIdx.x == 0) ctl->part_inv = st.fx_inv;
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -734,11 +739,16 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
     if (lane == 0) d.uk_part[blockIdx.x] = v;
   }
   if (V == kSmemESmemS || V == kGlobESmemS) {
-    Real* P = static_cast<Real*>(d.S_part) + (size_t)blockIdx.x * d.nxp;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      if (DEP == 1) P[i] = (Real)((float)st.Ss[i] * st.fx_inv);
-      else if (DEP == 4) P[i] = (Real)((double)st.Ss[i] * (double)st.fx_inv + (double)st.Ls[i] * (double)st.lo_inv);
-      else P[i] = (Real)st.Ss[i];
+    if (DEP == 1) {
+      // the raw int32 sums at the common scale ctl->part_inv
+      int* P = static_cast<int*>(d.S_part) + (size_t)blockIdx.x * d.nxp;
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) P[i] = (int)st.Ss[i];
+    } else {
+      Real* P = static_cast<Real*>(d.S_part) + (size_t)blockIdx.x * d.nxp;
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        if (DEP == 4) P[i] = (Real)((double)st.Ss[i] * (double)st.fx_inv + (double)st.Ls[i] * (double)st.lo_inv);
+        else P[i] = (Real)st.Ss[i];
+      }
     }
   }
 }
@@ -829,88 +839,124 @@ __device__ __forceinline__ void finish_step(const Dev& d, const double r[4], dou
   d.ring[(st - 1) % d.ring_n] = rec;
 }
 
+// Sums of four values over the 32 lanes of a warp (sum, sum, max, sum);
+// lane 0 holds the result.
+__device__ __forceinline__ void warp_reduce4(double v[4]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v[0] += __shfl_down_sync(kFull, v[0], o);
+    v[1] += __shfl_down_sync(kFull, v[1], o);
+    v[2] = fmax(v[2], __shfl_down_sync(kFull, v[2], o));
+    v[3] += __shfl_down_sync(kFull, v[3], o);
+  }
+}
+
+// Acc: element type of the per-CTA current rows (int: FP32 int32 sums at
+// the common scale ctl->part_inv, added exactly in int64; float/double: FP64
+// sums in a fixed row order).  kPartials: rows in S_part, else the FP64
+// global current S_glob.  On this part the FP64 pipe issues one warp
+// instruction per 16 cycles per SM, so the kernel keeps FP64 work off the
+// row sums (int64) and reduces its diagnostics in one warp.
 template <class Acc, bool kPartials>
 __global__ void __launch_bounds__(kFieldBlock) k_field(Dev d) {
   // 32 edges per CTA; the 8 warps each sum every 8th per-CTA partial row of
-  // those edges (coalesced), then warp 0 adds the 8 group sums in order, so
-  // the FP64 sum over rows has a fixed order
-  __shared__ double sh[128];
+  // those edges (coalesced), then warp 0 adds the 8 group sums in order
   __shared__ double grp[kFieldGroups][32];
+  __shared__ long long grp_i[kFieldGroups][32];
   __shared__ int s_last;
   Ctl* ctl = d.ctl;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;
   const int G = ctl->active_blocks;
+  constexpr bool kInt = std::is_integral<Acc>::value;
   if (kPartials) {
-    double S = 0.0;
-    if (i < d.nx) {
-      const Acc* P = static_cast<const Acc*>(d.S_part) + i;
-      const size_t pitch = d.nxp;
-      // four independent loads in flight, added in row order
-      int b = g;
-      for (; b + 3 * kFieldGroups < G; b += 4 * kFieldGroups) {
-        const double v0 = (double)P[(size_t)b * pitch];
-        const double v1 = (double)P[(size_t)(b + kFieldGroups) * pitch];
-        const double v2 = (double)P[(size_t)(b + 2 * kFieldGroups) * pitch];
-        const double v3 = (double)P[(size_t)(b + 3 * kFieldGroups) * pitch];
-        S += v0;
-        S += v1;
-        S += v2;
-        S += v3;
+    const Acc* P = static_cast<const Acc*>(d.S_part) + i;
+    const size_t pitch = d.nxp;
+    if (kInt) {
+      long long S = 0;
+      if (i < d.nx)
+        for (int b = g; b < G; b += kFieldGroups) S += (long long)P[(size_t)b * pitch];
+      grp_i[g][lane] = S;
+    } else {
+      double S = 0.0;
+      if (i < d.nx) {
+        // four independent loads in flight, added in row order
+        int b = g;
+        for (; b + 3 * kFieldGroups < G; b += 4 * kFieldGroups) {
+          const double v0 = (double)P[(size_t)b * pitch];
+          const double v1 = (double)P[(size_t)(b + kFieldGroups) * pitch];
+          const double v2 = (double)P[(size_t)(b + 2 * kFieldGroups) * pitch];
+          const double v3 = (double)P[(size_t)(b + 3 * kFieldGroups) * pitch];
+          S += v0;
+          S += v1;
+          S += v2;
+          S += v3;
+        }
+        for (; b < G; b += kFieldGroups) S += (double)P[(size_t)b * pitch];
       }
-      for (; b < G; b += kFieldGroups) S += (double)P[(size_t)b * pitch];
+      grp[g][lane] = S;
     }
-    grp[g][lane] = S;
     __syncthreads();
   }
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  if (g == 0 && i < d.nx) {
-    double S = 0.0;
-    if (kPartials) {
+  if (g == 0) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < d.nx) {
+      double S = 0.0;
+      if (kPartials && kInt) {
+        long long Si = 0;
 #pragma unroll
-      for (int k = 0; k < kFieldGroups; ++k) S += grp[k][lane];
-    } else {
-      S = d.S_glob[i];
-      d.S_glob[i] = 0.0;
+        for (int k = 0; k < kFieldGroups; ++k) Si += grp_i[k][lane];
+        S = (double)Si * (double)ctl->part_inv;
+      } else if (kPartials) {
+#pragma unroll
+        for (int k = 0; k < kFieldGroups; ++k) S += grp[k][lane];
+      } else {
+        S = d.S_glob[i];
+        d.S_glob[i] = 0.0;
+      }
+      const double J = d.jscale * S;
+      const double E = d.E[i] - d.dt * (J - d.j_m);  // Eq. 26 (j_m = 0 outside the co-rotating frame)
+      d.E[i] = E;
+      d.J[i] = J;
+      v[0] = E;
+      v[1] = J;
+      v[2] = fabs(E);
+      v[3] = 0.5 * E * E * d.dx;
     }
-    const double J = d.jscale * S;
-    const double E = d.E[i] - d.dt * (J - d.j_m);  // Eq. 26 (j_m = 0 outside the co-rotating frame)
-    d.E[i] = E;
-    d.J[i] = J;
-    v[0] = E;
-    v[1] = J;
-    v[2] = fabs(E);
-    v[3] = 0.5 * E * E * d.dx;
-  }
-  block_reduce4(v, sh);
-  if (threadIdx.x == 0) {
-    double* dp = d.diag_part + 4 * blockIdx.x;
-    dp[0] = v[0];
-    dp[1] = v[1];
-    dp[2] = v[2];
-    dp[3] = v[3];
-    __threadfence();
-    const unsigned t = atomicAdd(&ctl->field_ticket, 1u);
-    s_last = (t == gridDim.x - 1);
+    warp_reduce4(v);
+    if (lane == 0) {
+      double* dp = d.diag_part + 4 * blockIdx.x;
+      dp[0] = v[0];
+      dp[1] = v[1];
+      dp[2] = v[2];
+      dp[3] = v[3];
+      __threadfence();
+      const unsigned t = atomicAdd(&ctl->field_ticket, 1u);
+      s_last = (t == gridDim.x - 1);
+    }
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last || g != 0) return;
   __threadfence();
-  // last CTA: fold the per-CTA partials in a fixed order
+  // last CTA, warp 0: fold the per-CTA partials and the particle kernel's
+  // sums of gamma, each lane in a fixed order, then across the lanes
   double r[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    r[0] += __ldcg(d.diag_part + 4 * b + 0);
-    r[1] += __ldcg(d.diag_part + 4 * b + 1);
-    r[2] = fmax(r[2], __ldcg(d.diag_part + 4 * b + 2));
-    r[3] += __ldcg(d.diag_part + 4 * b + 3);
+  for (int b = lane; b < (int)gridDim.x; b += 32) {
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(d.diag_part + 4 * b));
+    const double2 c = __ldcg(reinterpret_cast<const double2*>(d.diag_part + 4 * b + 2));
+    r[0] += a.x;
+    r[1] += a.y;
+    r[2] = fmax(r[2], c.x);
+    r[3] += c.y;
   }
-  block_reduce4(r, sh);
-  double gs[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < G; b += blockDim.x) gs[0] += __ldcg(d.uk_part + b);
-  block_reduce4(gs, sh);
-  if (threadIdx.x == 0) {
+  double gs = 0.0;
+  for (int b = lane; b < G; b += 32) gs += __ldcg(d.uk_part + b);
+  warp_reduce4(r);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gs += __shfl_down_sync(kFull, gs, o);
+  if (lane == 0) {
     ctl->field_ticket = 0u;
-    finish_step(d, r, gs[0]);
+    finish_step(d, r, gs);
   }
 }
 
@@ -1509,7 +1555,8 @@ struct Launchers {
       k_compact_move<Real><<<64, 256, 0, st>>>(d);
     }
     if (d.variant == kSmemESmemS || d.variant == kGlobESmemS) {
-      k_field<Real, true><<<d.grid_field, kFieldBlock, 0, st>>>(d);
+      if (sizeof(Real) == 4 && d.push_dep == 1) k_field<int, true><<<d.grid_field, kFieldBlock, 0, st>>>(d);
+      else k_field<Real, true><<<d.grid_field, kFieldBlock, 0, st>>>(d);
     } else {
       k_field<Real, false><<<d.grid_field, kFieldBlock, 0, st>>>(d);
     }
