@@ -936,12 +936,13 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(Dev d) {
     }
   }
   __syncthreads();
-  if (!s_last || g != 0) return;
+  if (!s_last) return;
   __threadfence();
-  // last CTA, warp 0: fold the per-CTA partials and the particle kernel's
-  // sums of gamma, each lane in a fixed order, then across the lanes
+  // last CTA: each thread folds a fixed share of the per-CTA partials and of
+  // the particle kernel's sums of gamma, each warp reduces its lanes, and
+  // thread 0 adds the warps' results in warp order
   double r[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = lane; b < (int)gridDim.x; b += 32) {
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
     const double2 a = __ldcg(reinterpret_cast<const double2*>(d.diag_part + 4 * b));
     const double2 c = __ldcg(reinterpret_cast<const double2*>(d.diag_part + 4 * b + 2));
     r[0] += a.x;
@@ -950,13 +951,29 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(Dev d) {
     r[3] += c.y;
   }
   double gs = 0.0;
-  for (int b = lane; b < G; b += 32) gs += __ldcg(d.uk_part + b);
+  for (int b = threadIdx.x; b < G; b += blockDim.x) gs += __ldcg(d.uk_part + b);
   warp_reduce4(r);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) gs += __shfl_down_sync(kFull, gs, o);
   if (lane == 0) {
+    grp[0][g] = r[0];
+    grp[1][g] = r[1];
+    grp[2][g] = r[2];
+    grp[3][g] = r[3];
+    grp[4][g] = gs;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[4] = {0.0, 0.0, 0.0, 0.0}, ts = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t[0] += grp[0][w];
+      t[1] += grp[1][w];
+      t[2] = fmax(t[2], grp[2][w]);
+      t[3] += grp[3][w];
+      ts += grp[4][w];
+    }
     ctl->field_ticket = 0u;
-    finish_step(d, r, gs);
+    finish_step(d, t, ts);
   }
 }
 
