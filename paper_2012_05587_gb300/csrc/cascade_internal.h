@@ -54,7 +54,8 @@ struct Dev {
   // fields and reduction buffers
   double* E;           // E_{i+1/2}, nx
   double* J;           // J_{i+1/2}^{n+1/2}, nx
-  void* S_part;        // per-CTA charge-flux partials, [grid_push][nxp] (Acc)
+  void* S_part;        // per-CTA charge-flux partials, [grid_push][nxp]: int32 at the scale
+                       // ctl->part_inv (FP32, one-word accumulator), else Real
   double* S_glob;      // nx, when the partials do not fit in shared memory
   double* uk_part;     // per-CTA sum of gamma, [grid_push]
   double* diag_part;   // per-CTA field diagnostics of the field kernel, [grid_field][4]
