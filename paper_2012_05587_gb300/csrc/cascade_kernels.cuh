@@ -1520,12 +1520,16 @@ struct Launchers {
     d.push_stage = 0;
     if (sizeof(Real) == 4 && variant == kSmemESmemS && dep == 1 && !d.open_bc &&
         env_int("CASCADE_PUSH_STAGE", 1) == 1) {
-      // the staging area must fit beside E and the accumulator (1 KB left
-      // for the kernel's static shared memory)
+      // the staging area must fit beside E, the accumulator and the
+      // kernel's static shared memory
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      if (smem_bytes(d.nx, variant, dep) + kStageBytesPerThread * block + 1024 <= (size_t)optin) d.push_stage = 1;
+      cudaFuncAttributes fa{};
+      const cudaError_t ea = cudaFuncGetAttributes(&fa, PushTable<Real>::get(variant, dep, fast != 0, false, true));
+      if (ea != cudaSuccess) return ea;
+      if (smem_bytes(d.nx, variant, dep) + kStageBytesPerThread * block + fa.sharedSizeBytes <= (size_t)optin)
+        d.push_stage = 1;
     }
     const size_t smem = push_smem(d);
     const void* fn = push_fn(d);
@@ -1625,14 +1629,22 @@ struct Launchers {
     if (shape < 0 || shape > 3) shape = 3;
     const int threads = batch_threads(shape);
     // FP32: stage the particles through shared memory where the staging area
-    // fits beside E and the accumulator (1 KB left for static shared memory)
+    // fits beside E, the accumulator and the kernel's static shared memory
+    // (per CTA, and for the CTAs per SM of the launch shape, with the 1 KB
+    // the system reserves per CTA)
     int stage = 0;
     if (sizeof(Real) == 4 && env_int("CASCADE_BATCH_STAGE", 1) == 1) {
-      int dev = 0, optin = 0;
+      int dev = 0, optin = 0, per_sm_max = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      const size_t need = (sm + kStageBytesPerThread * threads) * batch_minb(shape) + 1024;
-      if (need <= (size_t)optin) stage = 1;
+      cudaDeviceGetAttribute(&per_sm_max, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+      cudaFuncAttributes fa{};
+      const cudaError_t ea = cudaFuncGetAttributes(&fa, batch_push_fn(dp, shape, true));
+      if (ea != cudaSuccess) return ea;
+      const size_t per_cta = sm + kStageBytesPerThread * threads;
+      if (per_cta + fa.sharedSizeBytes <= (size_t)optin &&
+          (per_cta + fa.sharedSizeBytes + 1024) * batch_minb(shape) <= (size_t)per_sm_max)
+        stage = 1;
     }
     const size_t smem_total = sm + (stage ? kStageBytesPerThread * threads : 0);
     const void* fn = batch_push_fn(dp, shape, stage != 0);
