@@ -114,7 +114,8 @@ def test_fp64_parity_ragged_grids(nx, ppc, lpp):
     that are not multiples of four, in-place (l_pp = 0) and long flights."""
     p = dict(nx=nx, ppc=ppc, dx=0.07, dt=0.03, n0=1.0, u_spread=0.05, seed=11 + nx, E0=12.0,
              gamma_thr=20.0, eps_gamma=8.0, l_pp=lpp, particle_cap=1 << 16, precision="fp64")
-    check_fp64_parity(p, 400, 20, min_horizon=60)
+    hz, _, _ = check_fp64_parity(p, 400, 20, min_horizon=60)
+    print(f"parity horizon (Nx = {nx}): step {hz} of 400")
 
 
 def test_fp64_hand_built_emission_is_exact():
