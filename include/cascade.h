@@ -215,7 +215,10 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
 
 /* Batch of n members created from params[0..n-1] (all in the Section 3
  * initial state); max_nx is the largest member grid; every member starts
- * with zero steps to do. */
+ * with zero steps to do.  Every member is checked on the host before any
+ * device work: the single-cascade parameter domain, one precision class
+ * for all, periodic grids; a failure returns CASCADE_ERR_INVALID_ARG and
+ * cascade_last_error_message names the member. */
 int cascade_batch_create(const cascade_params* params, int32_t n, size_t hbm_budget, void* cuda_stream,
                          cascade_batch_t** out);
 

@@ -746,8 +746,10 @@ extern "C" {
 int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max_nx, size_t hbm_budget,
                                void* cuda_stream, cascade_batch_t** out) {
   if (!out || max_slots < 1 || max_nx < 2 ||
-      (precision != CASCADE_FP64 && precision != CASCADE_FP32_MIXED && precision != CASCADE_FP32_MIXED_FINE))
+      (precision != CASCADE_FP64 && precision != CASCADE_FP32_MIXED && precision != CASCADE_FP32_MIXED_FINE)) {
+    snprintf(g_msg, sizeof(g_msg), "batch: out is required, max_slots >= 1, max_nx >= 2, known precision");
     return CASCADE_ERR_INVALID_ARG;
+  }
   *out = nullptr;
   cascade_batch_t* b = new (std::nothrow) cascade_batch_t();
   if (!b) return CASCADE_ERR_OOM;
@@ -878,10 +880,29 @@ int cascade_batch_admit(cascade_batch_t* b, const cascade_params* params, int32_
 
 int cascade_batch_create(const cascade_params* params, int32_t n, size_t hbm_budget, void* cuda_stream,
                          cascade_batch_t** out) {
-  if (!params || n < 1 || !out) return CASCADE_ERR_INVALID_ARG;
+  if (!params || n < 1 || !out) {
+    snprintf(g_msg, sizeof(g_msg), "batch: params, n >= 1 and out are required");
+    return CASCADE_ERR_INVALID_ARG;
+  }
+  // every member is checked on the host before any device work
   int max_nx = 2;
   for (int i = 0; i < n; ++i) {
-    if (!same_kernel_class(params[i].precision, params[0].precision)) return CASCADE_ERR_INVALID_ARG;
+    const int rc = validate(&params[i]);
+    if (rc) {
+      char why[sizeof(g_msg)];
+      snprintf(why, sizeof(why), "%s", g_msg);
+      snprintf(g_msg, sizeof(g_msg), "member %d: %s", i, why);
+      return rc;
+    }
+    if (!same_kernel_class(params[i].precision, params[0].precision)) {
+      snprintf(g_msg, sizeof(g_msg), "member %d: precision %d differs from member 0's %d", i, params[i].precision,
+               params[0].precision);
+      return CASCADE_ERR_INVALID_ARG;
+    }
+    if (params[i].open_bc) {
+      snprintf(g_msg, sizeof(g_msg), "member %d: batch members are periodic (open_bc = 0)", i);
+      return CASCADE_ERR_INVALID_ARG;
+    }
     if (params[i].nx > max_nx) max_nx = params[i].nx;
   }
   cascade_batch_t* b = nullptr;

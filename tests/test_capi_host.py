@@ -84,3 +84,27 @@ def test_create_without_device_fails_cleanly():
     with pytest.raises(capi.CascadeError) as ei:
         capi.cascade_create(W.small_cascade())
     assert ei.value.status == capi.CASCADE_ERR_CUDA
+
+
+@pytest.mark.parametrize("members,why", [
+    ([dict(eps_gamma=1.5)], "member 0: invalid parameters: eps_gamma"),
+    ([{}, dict(precision="fp64")], "member 1: precision"),
+    ([{}, {}, dict(open_bc=1)], "member 2: batch members are periodic"),
+])
+def test_batch_members_validated_before_device_work(members, why):
+    """A batch checks every member on the host (the same domain as a single
+    cascade, one precision class, periodic grids) before touching a device."""
+    ps = [dict(W.small_cascade(precision="fp32"), **m) for m in members]
+    with pytest.raises(capi.CascadeError) as ei:
+        capi.cascade_batch_create(ps, 0, 0)
+    assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
+    assert why in str(ei.value)
+
+
+def test_batch_slots_validated():
+    with pytest.raises(capi.CascadeError) as ei:
+        capi.cascade_batch_create_slots(0, "fp32", 1024, 0, 0)
+    assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
+    with pytest.raises(capi.CascadeError) as ei:
+        capi.cascade_batch_create_slots(4, "fp32", 1, 0, 0)
+    assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
