@@ -304,7 +304,10 @@ int cascade_footprint(const cascade_params* params, int32_t* n_pp_out, size_t* d
 /* Human-readable text of a status code (static storage). */
 const char* cascade_status_string(int status);
 
-/* Detail of the last failure on the calling thread (static, thread-local). */
+/* Detail of the last failure on the calling thread (static, thread-local).
+ * Every entry point except the destroy calls clears it on entry, so it
+ * describes the most recent call only; it is empty when that call set no
+ * detail. */
 const char* cascade_last_error_message(void);
 
 #ifdef __cplusplus

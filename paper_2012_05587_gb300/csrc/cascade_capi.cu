@@ -386,6 +386,7 @@ int create_seeded(const cascade_params* params, void* cuda_stream, bool batch_me
 extern "C" {
 
 int cascade_set_allocator(cascade_alloc_fn alloc_fn, cascade_free_fn free_fn, void* ctx) {
+  g_msg[0] = '\0';  // a message describes this call only
   if ((alloc_fn == nullptr) != (free_fn == nullptr)) return CASCADE_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_alloc_mu);
   g_alloc = alloc_fn;
@@ -395,6 +396,7 @@ int cascade_set_allocator(cascade_alloc_fn alloc_fn, cascade_free_fn free_fn, vo
 }
 
 int cascade_create(const cascade_params* params, void* cuda_stream, cascade_t** out) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!out) return CASCADE_ERR_INVALID_ARG;
   return create_seeded(params, cuda_stream, false, out);
 }
@@ -403,6 +405,7 @@ int cascade_create_from_state(const cascade_params* params, int64_t n_elec, cons
                               const double* off_e, const double* u_e, int64_t n_posi, const int32_t* cell_p,
                               const double* off_p, const double* u_p, const double* E_host, void* cuda_stream,
                               cascade_t** out) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!out || n_elec < 0 || n_posi < 0) return CASCADE_ERR_INVALID_ARG;
   if ((n_elec > 0 && (!cell_e || !off_e || !u_e)) || (n_posi > 0 && (!cell_p || !off_p || !u_p)))
     return CASCADE_ERR_INVALID_ARG;
@@ -425,6 +428,7 @@ int cascade_create_from_state(const cascade_params* params, int64_t n_elec, cons
 }
 
 int cascade_step(cascade_t* h, int32_t nsteps) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!h || nsteps < 0) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   int left = nsteps;
@@ -445,6 +449,7 @@ int cascade_step(cascade_t* h, int32_t nsteps) {
 }
 
 int cascade_sync(cascade_t* h) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!h) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   Ctl c;
@@ -455,6 +460,7 @@ int cascade_sync(cascade_t* h) {
 
 int cascade_diag(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t* n_out, double* E_host,
                  double* J_host) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!h || max < 0 || (max > 0 && !host_out)) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   Ctl c;
@@ -479,6 +485,7 @@ int cascade_diag(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t* n
 }
 
 int cascade_gauss(cascade_t* h, double* resid_out) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!h || !resid_out) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   cudaError_t e = h->p.precision == CASCADE_FP64 ? gauss_fp64(h->d, h->rho_dx, h->scalar, h->stream)
@@ -490,6 +497,7 @@ int cascade_gauss(cascade_t* h, double* resid_out) {
 }
 
 int cascade_counts(cascade_t* h, int64_t* n_elec, int64_t* n_posi, int64_t* n_photon, int64_t* step) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!h) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   Ctl c;
@@ -504,6 +512,7 @@ int cascade_counts(cascade_t* h, int64_t* n_elec, int64_t* n_posi, int64_t* n_ph
 
 int cascade_histogram(cascade_t* h, int32_t species, int32_t quantity, int32_t nbins, double lo, double hi,
                       int64_t* counts_host) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!h || species < 0 || species > 1 || quantity < 0 || quantity > 2 || nbins < 1 || nbins > 65536 ||
       !(hi > lo) || !counts_host)
     return CASCADE_ERR_INVALID_ARG;
@@ -527,6 +536,7 @@ int cascade_histogram(cascade_t* h, int32_t species, int32_t quantity, int32_t n
 
 int cascade_particles(cascade_t* h, int32_t species, int64_t max, int32_t* cell, double* off, double* u,
                       int64_t* n_out) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!h || species < 0 || species > 1 || max < 0) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   Ctl c;
@@ -554,6 +564,7 @@ int cascade_particles(cascade_t* h, int32_t species, int64_t max, int32_t* cell,
 }
 
 int cascade_set_timing(cascade_t* h, int32_t enable) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!h) return CASCADE_ERR_INVALID_ARG;
   h->timing = enable != 0;
   return CASCADE_OK;
@@ -561,6 +572,7 @@ int cascade_set_timing(cascade_t* h, int32_t enable) {
 
 int cascade_timing(cascade_t* h, double* particle_kernel_ms, int64_t* particle_kernel_launches,
                    int64_t* kernels_launched) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!h) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -594,6 +606,7 @@ int cascade_destroy(cascade_t* h) {
 }
 
 int cascade_footprint(const cascade_params* params, int32_t* n_pp_out, size_t* device_bytes_out) {
+  g_msg[0] = '\0';  // a message describes this call only
   int rc = validate(params);
   if (rc) return rc;
   const Plan pl = plan_of(params);
@@ -745,6 +758,7 @@ extern "C" {
 
 int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max_nx, size_t hbm_budget,
                                void* cuda_stream, cascade_batch_t** out) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!out || max_slots < 1 || max_nx < 2 ||
       (precision != CASCADE_FP64 && precision != CASCADE_FP32_MIXED && precision != CASCADE_FP32_MIXED_FINE)) {
     snprintf(g_msg, sizeof(g_msg), "batch: out is required, max_slots >= 1, max_nx >= 2, known precision");
@@ -825,6 +839,7 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
 }
 
 int cascade_batch_admit(cascade_batch_t* b, const cascade_params* params, int32_t nsteps, int32_t* slot_out) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!b || !params || nsteps < 0) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(b->device);
   int rc = validate(params);
@@ -880,6 +895,7 @@ int cascade_batch_admit(cascade_batch_t* b, const cascade_params* params, int32_
 
 int cascade_batch_create(const cascade_params* params, int32_t n, size_t hbm_budget, void* cuda_stream,
                          cascade_batch_t** out) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!params || n < 1 || !out) {
     snprintf(g_msg, sizeof(g_msg), "batch: params, n >= 1 and out are required");
     return CASCADE_ERR_INVALID_ARG;
@@ -921,6 +937,7 @@ int cascade_batch_create(const cascade_params* params, int32_t n, size_t hbm_bud
 }
 
 int cascade_batch_step(cascade_batch_t* b, const int32_t* nsteps_each) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!b || !nsteps_each) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(b->device);
   // current remaining counts, then add the new targets
@@ -949,12 +966,14 @@ int cascade_batch_step(cascade_batch_t* b, const int32_t* nsteps_each) {
 }
 
 int cascade_batch_run(cascade_batch_t* b, int32_t nsteps) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!b || nsteps < 0) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(b->device);
   return batch_enqueue(b, nsteps);
 }
 
 int cascade_batch_poll(cascade_batch_t* b, int32_t* done_slots, int32_t max, int32_t* n_out, int32_t wait) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!b || max < 0 || (max > 0 && !done_slots)) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(b->device);
   int best = -1;
@@ -1001,6 +1020,7 @@ int batch_settle(cascade_batch_t* b, int slot) {
 
 int cascade_batch_diag(cascade_batch_t* b, int32_t slot, cascade_diag_t* host_out, int32_t max, int32_t* n_out,
                        double* E_host, double* J_host) {
+  g_msg[0] = '\0';  // a message describes this call only
   int rc = batch_member_check(b, slot);
   if (rc) return rc;
   cudaSetDevice(b->device);
@@ -1010,6 +1030,7 @@ int cascade_batch_diag(cascade_batch_t* b, int32_t slot, cascade_diag_t* host_ou
 
 int cascade_batch_counts(cascade_batch_t* b, int32_t slot, int64_t* n_elec, int64_t* n_posi, int64_t* n_photon,
                          int64_t* step) {
+  g_msg[0] = '\0';  // a message describes this call only
   int rc = batch_member_check(b, slot);
   if (rc) return rc;
   cudaSetDevice(b->device);
@@ -1018,6 +1039,7 @@ int cascade_batch_counts(cascade_batch_t* b, int32_t slot, int64_t* n_elec, int6
 }
 
 int cascade_batch_release(cascade_batch_t* b, int32_t slot) {
+  g_msg[0] = '\0';  // a message describes this call only
   int rc = batch_member_check(b, slot);
   if (rc) return rc;
   cudaSetDevice(b->device);
@@ -1036,6 +1058,7 @@ int cascade_batch_release(cascade_batch_t* b, int32_t slot) {
 }
 
 int cascade_batch_info(cascade_batch_t* b, int32_t* slots, int32_t* occupied, size_t* bytes_in_use) {
+  g_msg[0] = '\0';  // a message describes this call only
   if (!b) return CASCADE_ERR_INVALID_ARG;
   int occ = 0;
   for (cascade_t* h : b->members) occ += h != nullptr;

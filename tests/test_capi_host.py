@@ -108,3 +108,12 @@ def test_batch_slots_validated():
     with pytest.raises(capi.CascadeError) as ei:
         capi.cascade_batch_create_slots(4, "fp32", 1, 0, 0)
     assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
+
+
+def test_error_message_describes_the_latest_call_only():
+    lib = capi.load()
+    with pytest.raises(capi.CascadeError):
+        capi.cascade_footprint(dict(W.small_cascade(), eps_gamma=1.5))
+    assert b"eps_gamma" in lib.cascade_last_error_message()
+    capi.cascade_footprint(W.small_cascade())
+    assert lib.cascade_last_error_message() == b""
