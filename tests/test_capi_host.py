@@ -117,3 +117,11 @@ def test_error_message_describes_the_latest_call_only():
     assert b"eps_gamma" in lib.cascade_last_error_message()
     capi.cascade_footprint(W.small_cascade())
     assert lib.cascade_last_error_message() == b""
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the compiled library the binding raises."""
+    monkeypatch.setattr(capi, "_lib", None)
+    monkeypatch.setattr(capi, "LIB_PATH", str(tmp_path / "libcascade.so"))
+    with pytest.raises(ImportError, match="missing"):
+        capi.load()
