@@ -48,10 +48,12 @@ def _fp64_one_at_a_time(params: list, steps_of) -> dict:
 def run_batch(args) -> int:
     import torch
 
-    from paper_2012_05587_gb300 import CascadeBatch, workloads as W
+    from paper_2012_05587_gb300 import CascadeBatch, capi, workloads as W
 
     prec = args.precision
     scan = W.batch_scan(args.batch_n, precision=prec, steps=args.batch_steps)
+    footprint = sum(capi.cascade_footprint(p)[1] for p in scan)
+    predicted = sum(W.predicted_particles(p) for p in scan)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     b = CascadeBatch(scan)
@@ -91,6 +93,7 @@ def run_batch(args) -> int:
                                "{8,16,32,64}, E0 and gamma_thr log-U[10,1000], eps = gamma_thr/2, l_pp U[0.2,2]), "
                                f"{args.batch_steps} steps each, {prec}, one launch per kernel per step",
                    "members_over_capacity": over, "create_s": t_create, "wall_s": wall,
+                   "device_footprint_bytes": footprint, "predicted_particles_at_screening": predicted,
                    "pairs_created_per_particle_step": pairs / ps if ps else None,
                    "photons_emitted_per_particle_step": photons / ps if ps else None},
         "fp64_one_at_a_time": dict(fp64, per_request_s=None,
