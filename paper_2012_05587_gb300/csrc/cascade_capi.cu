@@ -470,6 +470,10 @@ int cascade_diag(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t* n
   const long long n = kept < max ? kept : max;
   const long long first = c.step - n;  // records of steps first+1 .. c.step
   long long done = 0;
+  if (n == 1) {  // the latest record came with the counters: no second copy
+    host_out[0] = c.last;
+    done = 1;
+  }
   while (done < n) {
     const long long slot = (first + done) % h->d.ring_n;
     long long run = h->d.ring_n - slot;

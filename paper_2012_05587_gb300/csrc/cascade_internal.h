@@ -30,6 +30,7 @@ struct Ctl {
   unsigned long long n_holes[2];  // departed (hole-list entries, may exceed the list)
   unsigned long long na[2];       // holes below the new count
   unsigned long long nb[2];       // live particles at or above the new count
+  cascade_diag_t last;            // the latest per-step record (also in the ring), read with the counters
 };
 
 // Everything a kernel needs about one cascade, passed by value.

@@ -837,6 +837,7 @@ __device__ __forceinline__ void finish_step(const Dev& d, const double r[4], dou
   rec.n_pairs_total = ctl->pairs_total;
   rec.n_emit_multi = ctl->emit_multi;
   d.ring[(st - 1) % d.ring_n] = rec;
+  ctl->last = rec;
 }
 
 // Sums of four values over the 32 lanes of a warp (sum, sum, max, sum);
@@ -1421,7 +1422,10 @@ __global__ void k_gauss_reduce(Dev d, const double* rho_dx, double* out) {
   if (threadIdx.x == 0) {
     *out = v[2];
     const long long st = d.ctl->step;
-    if (st > 0) d.ring[(st - 1) % d.ring_n].gauss_resid = v[2];
+    if (st > 0) {
+      d.ring[(st - 1) % d.ring_n].gauss_resid = v[2];
+      d.ctl->last.gauss_resid = v[2];
+    }
   }
 }
 
