@@ -63,3 +63,31 @@ def test_empty_state_follows_the_background_current(precision):
     assert np.allclose(E, E0 + steps * dt * jm, rtol=0, atol=1e-12)
     assert np.array_equal(E, E_ref)
     assert np.allclose(d["E_mean"], d_ref["E_mean"], rtol=0, atol=1e-13)
+
+
+def test_photon_ring_overflow_is_reported():
+    """A photon ring smaller than one step's emissions: the photons that do not
+    fit are dropped and the run reports CASCADE_ERR_PHOTON_CAPACITY (the ring
+    index is checked before every append)."""
+    from paper_2012_05587_gb300 import CascadeError, capi, workloads as W
+
+    p = dict(W.small_cascade(), photon_cap=64)
+    with Cascade(p) as c:
+        c.step(120)  # the seed reaches gamma_thr after t_a = 2 (40 steps); 8192 leptons emit together
+        with pytest.raises(CascadeError) as ei:
+            c.sync()
+        assert ei.value.status == capi.CASCADE_ERR_PHOTON_CAPACITY
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_runaway_energy_is_reported(precision):
+    """A field so strong that one push takes u past 1e30: the particle kernel
+    flags CASCADE_ERR_NONFINITE instead of emitting from a meaningless gamma."""
+    from paper_2012_05587_gb300 import CascadeError, capi, workloads as W
+
+    p = dict(W.small_cascade(precision=precision), E0=1e33)
+    with Cascade(p) as c:
+        c.step(3)
+        with pytest.raises(CascadeError) as ei:
+            c.sync()
+        assert ei.value.status == capi.CASCADE_ERR_NONFINITE
