@@ -120,3 +120,19 @@ def test_open_boundaries_rejected_in_batches():
         with pytest.raises(CascadeError) as ei:
             b.admit(p, 10)
         assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
+
+
+def test_open_boundaries_on_a_grid_beyond_shared_memory():
+    """Nx = 40000 in FP32: E does not fit beside the accumulator, so the open-
+    boundary particle kernel reads E through L1.  The Section 7 state (j_m,
+    rho_GJ, open ends), 100 steps against the oracle: E per edge, the interior
+    Gauss residual and the species counts."""
+    p = W.corotating(nx=40000, precision="fp32", gamma_thr=60.0, eps_gamma=6.0, dt=0.02)
+    state, E = W.corotating_state(p)
+    r_ref, r_gpu, snaps = run_pair(p, state, E, 100, chunk=100)
+    done, Eg, _, Er, _, gres = snaps[-1]
+    scale = max(np.abs(Er).max(), 1e-12)
+    assert np.abs(Eg - Er).max() <= 2e-4 * scale
+    assert gres <= 1e-4 * max(1.0, scale)
+    for k in ("n_elec", "n_posi"):
+        assert np.abs(r_gpu[k] - r_ref[k]).max() <= 2
