@@ -21,6 +21,7 @@ ALL_PINS = [
     pins.test_single_particle_uniform_field_second_order,
     pins.test_electron_moves_against_field,
     pins.test_gauss_and_charge_conservation_with_qed,
+    pins.test_mean_current_and_field_of_a_hand_built_state,
     pins.test_cold_uniform_mode_frequency,
     pins.test_relativistic_uniform_mode_period,
     pins.test_standing_langmuir_wave,
@@ -66,6 +67,9 @@ MUTANTS = [
     ("photon_direction_lost", "s->ph_dir[s->nph] = (int8_t)(sgn > 0 ? 1 : -1);", "s->ph_dir[s->nph] = 1;"),
     ("kinetic_energy_weight", "uk += s->w * s->gam[p];", "uk += s->gam[p];"),
     ("field_energy_half", "ue += 0.5 * s->E[i] * s->E[i] * s->p.dx;", "ue += s->E[i] * s->E[i] * s->p.dx;"),
+    ("mean_current_half", "d->J_mean = sj / nx;", "d->J_mean = 0.5 * sj / nx;"),
+    ("field_max_from_edge_0", "double a = fabs(s->E[i]);", "double a = fabs(s->E[0]);"),
+    ("field_max_signed", "double a = fabs(s->E[i]);", "double a = s->E[i];"),
     ("background_current_sign", "s->E[i] = s->E[i] - dt * (s->J[i] - s->p.j_m);",
      "s->E[i] = s->E[i] - dt * (s->J[i] + s->p.j_m);"),
     ("background_charge_sign", "(s->rho_dx[i] - s->p.rho_gj * s->p.dx)", "(s->rho_dx[i] + s->p.rho_gj * s->p.dx)"),

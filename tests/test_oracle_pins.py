@@ -121,6 +121,38 @@ def test_gauss_and_charge_conservation_with_qed(lib=None):
     assert np.array_equal(d["n_elec"], d["n_posi"])
 
 
+def test_mean_current_and_field_of_a_hand_built_state(lib=None):
+    """The per-step field diagnostics on a state whose values are fixed by
+    definitions outside the oracle: two charges moving at known speed in a
+    region where the field is zero (so they are not pushed), one of them
+    crossing a node.
+
+    * <J> is the domain average of the current density of the moving
+      macro-particles, sum over particles of q w v / L (w = n0 dx / ppc per
+      unit area, L = nx dx), whatever the deposit stencil;
+    * <E> then follows from Ampere's law averaged over the periodic domain,
+      <E>^{n+1} = <E>^n - dt <J>;
+    * max |E| is attained at an edge other than 0 and by a negative value."""
+    p = dict(nx=8, ppc=1, dx=0.1, dt=0.01, n0=1.0, u_spread=0.0, seed=1, E0=0.0,
+             gamma_thr=1e9, eps_gamma=10.0, l_pp=0.0)
+    E = np.array([1.0, -5.0, 0.0, 0.0, 3.5, 0.0, 0.0, 2.0])
+    # a positron at v = +0.6 (u = 3/4) and an electron at v = -0.8 (u = -4/3)
+    # that crosses the node at x = 6 dx; both sit between edges where E = 0
+    u = np.array([0.75, -4.0 / 3.0])
+    q = np.array([1, -1])
+    o = oracle.Oracle.from_state(p, [3, 6], [0.2, 0.03], u, q, E=E, lib_path=lib)
+    d = o.step(1)
+    w, L = p["n0"] * p["dx"] / p["ppc"], p["nx"] * p["dx"]
+    v = u / np.sqrt(1.0 + u * u)
+    J_mean = float((q * w * v).sum() / L)
+    assert J_mean == pytest.approx(0.175, rel=1e-15)
+    assert d["J_mean"][0] == pytest.approx(J_mean, rel=1e-12)
+    assert d["E_mean"][0] == pytest.approx(E.mean() - p["dt"] * J_mean, rel=1e-12)
+    assert d["E_absmax"][0] == pytest.approx(5.0, rel=1e-15)
+    st = o.particles()
+    assert np.array_equal(st["cell"], [3, 5])  # the electron crossed into cell 5
+
+
 def test_cold_uniform_mode_frequency(lib=None):
     """Linear cold uniform mode of a pair plasma: 2 sin(w dt/2)/dt = sqrt(2 n0)."""
     dt = 0.01
