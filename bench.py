@@ -39,10 +39,12 @@ METRIC = "particle-steps/s incl. deposit+QED (batched FP32 vs plain FP64), % HBM
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = {"fp32": 24, "fp64": 40}
 # DRAM bytes (read + write) per particle-step of the FP32 particle kernel (the
-# form that stages its particles through shared memory), from one ncu capture
-# of this kernel on a smaller post-screening case of the same grid
-# (profiles/k_push_fp32_post_screening.md: 785.3 MB for 3.487e7
-# particle-steps); traffic grows in proportion to the particles processed.
+# form that stages its particles through shared memory): dram__bytes_read.sum +
+# dram__bytes_write.sum = 418.6 + 366.7 MB for 3.487e7 particle-steps in one
+# launch, from "ncu --set full --clock-control none -k regex:k_push -s 203 -c 2
+# python bench.py --steps 10 --warmup 3 --prep 200 --ppc 8 --cap 25000000
+# --no-e2e --no-cpu" (a post-screening case of the same grid, 8 + 8 seed
+# particles per cell); traffic grows in proportion to the particles processed.
 MEASURED_DRAM_BYTES_PER_PARTICLE_STEP = {"fp32": 22.52}
 # The FP64 particle kernel is bound by the FP64 pipe, not by HBM: ncu counted
 # 45,085,174 FP64-pipe warp instructions for 34,865,152 particle-steps

@@ -261,9 +261,10 @@ int cascade_batch_destroy(cascade_batch_t* b);
 /* Largest grid cascade_gauss_noalloc accepts. */
 #define CASCADE_NOALLOC_MAX_NX 65536
 
-/* Gauss's-law residual max_i |E_{i+1/2} - E_{i-1/2} - dx rho_i| of a state
- * held by the caller, computed without allocating any memory.  The paper has
- * no counterpart: this is a library service, the same check as cascade_gauss
+/* Gauss's-law residual max_i |E_{i+1/2} - E_{i-1/2} - dx (rho_i - rho_GJ)|
+ * (Eq. 25; rho_GJ = 0 outside the co-rotating frame) of a state held by the
+ * caller, computed without allocating any memory.  The paper has no
+ * counterpart: this is a library service, the same check as cascade_gauss
  * but on the caller's buffers.  It exists for callers that cannot allocate
  * device memory: applications that reserve all device memory for their own
  * pool at start-up and forbid libraries to allocate, plug-ins whose host
@@ -274,22 +275,28 @@ int cascade_batch_destroy(cascade_batch_t* b);
  * the process exits.
  *   nx          cells, 2 .. CASCADE_NOALLOC_MAX_NX (otherwise
  *               CASCADE_ERR_INVALID_ARG, with a message naming the limit)
- *   dx          cell size (the residual is in units of E)
+ *   dx          cell size (> 0); the residual is in units of E
  *   w           macro-particle weight n0 dx / ppc
- *   precision   CASCADE_FP64: offsets are double; otherwise float
+ *   rho_gj      background charge density (0 outside the co-rotating frame)
+ *   open_bc     0: periodic (node nx is node 0); 1: open boundaries (the
+ *               charge beyond node nx - 1 is not kept, node 0 is not checked)
+ *   precision   CASCADE_FP64: offsets are double; CASCADE_FP32_MIXED and
+ *               CASCADE_FP32_MIXED_FINE: offsets are float
  *   n_elec, cell_e, off_e / n_posi, cell_p, off_p
  *               particle counts and DEVICE arrays (cell int32 in [0, nx),
- *               offset in [0, 1)), read only
+ *               offset in [0, 1); a cell outside the grid, such as the -1 of
+ *               a departed particle, is skipped), read only
  *   E           DEVICE array of nx doubles, E_{i+1/2} at [i], read only
  *   resid_out   HOST double receiving the residual
- *   cuda_stream stream the work is issued on; the call synchronises it
+ *   cuda_stream stream the work is issued on; the call synchronises it and
+ *               copies the result to the host before returning
  * The first call on a device looks up the device address of the scratch
  * array (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call shares the one array and clears it first: calls that
  * overlap on the GPU (other streams or threads at the same time) race on it,
  * so serialise them.  No cudaMalloc, cudaFree or allocating library call is
  * made. */
-int cascade_gauss_noalloc(int32_t nx, double dx, double w, int32_t precision,
+int cascade_gauss_noalloc(int32_t nx, double dx, double w, double rho_gj, int32_t open_bc, int32_t precision,
                           int64_t n_elec, const int32_t* cell_e, const void* off_e,
                           int64_t n_posi, const int32_t* cell_p, const void* off_p,
                           const double* E, double* resid_out, void* cuda_stream);

@@ -71,10 +71,17 @@ def lambert_growth_rate(E0: float, gamma_thr: float, eps_gamma: float) -> float:
 
 
 def renewal_growth_rate(E0: float, gamma_thr: float, eps_gamma: float, delay: float = 0.0) -> float:
-    """Growth rate of the threshold cascade in a uniform, unscreened field:
-    exp(-G (T2 + d)) + exp(-G (T3 + d)) = 1 - exp(-G T1), with T1 the
-    re-emission time of a lepton at threshold and T2, T3 the times for a new
-    pair member to reach threshold along and against the field."""
+    """Exact growth rate of the threshold cascade in a frozen uniform field.
+
+    In a uniform field u grows linearly, so a lepton at the threshold
+    (u_thr = sqrt(gamma_thr^2 - 1)) that recoils to gamma_thr - eps (u_r) emits
+    again after T1 = (u_thr - u_r) / E0.  Each photon becomes, after the flight
+    delay d, two leptons of gamma = eps / 2 (u_p) moving along it (Section 2):
+    the one whose charge the field accelerates forward reaches the threshold
+    after T2 = (u_thr - u_p) / E0, the other turns around and needs
+    T3 = (u_thr + u_p) / E0.  Counting descendants (Euler-Lotka) gives
+        exp(-G (T2 + d)) + exp(-G (T3 + d)) = 1 - exp(-G T1).
+    For f << 1 and d = 0 this reduces to Eq. 3."""
     from scipy.optimize import brentq
 
     ut = np.sqrt(gamma_thr ** 2 - 1.0)

@@ -104,7 +104,7 @@ def load() -> ctypes.CDLL:
             "cascade_footprint": ([P(cascade_params), P(i32), P(ctypes.c_size_t)], ctypes.c_int),
             "cascade_set_timing": ([vp, i32], ctypes.c_int),
             "cascade_timing": ([vp, P(f64), P(i64), P(i64)], ctypes.c_int),
-            "cascade_gauss_noalloc": ([i32, f64, f64, i32, i64, vp, vp, i64, vp, vp, vp, P(f64), vp],
+            "cascade_gauss_noalloc": ([i32, f64, f64, f64, i32, i32, i64, vp, vp, i64, vp, vp, vp, P(f64), vp],
                                       ctypes.c_int),
             "cascade_batch_create_slots": ([i32, i32, i32, ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
             "cascade_batch_create": ([P(cascade_params), i32, ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
@@ -290,14 +290,15 @@ def cascade_timing(h) -> dict:
 
 
 def cascade_gauss_noalloc(nx: int, dx: float, w: float, precision: int, n_elec: int, cell_e: int, off_e: int,
-                          n_posi: int, cell_p: int, off_p: int, E: int, stream: int = 0) -> float:
+                          n_posi: int, cell_p: int, off_p: int, E: int, stream: int = 0, rho_gj: float = 0.0,
+                          open_bc: int = 0) -> float:
     """Gauss residual of caller-held DEVICE buffers (pointers as ints); the
     library allocates nothing for this call."""
     r = ctypes.c_double()
     check("cascade_gauss_noalloc", load().cascade_gauss_noalloc(
-        int(nx), float(dx), float(w), int(precision), int(n_elec), ctypes.c_void_p(cell_e),
-        ctypes.c_void_p(off_e), int(n_posi), ctypes.c_void_p(cell_p), ctypes.c_void_p(off_p),
-        ctypes.c_void_p(E), ctypes.byref(r), ctypes.c_void_p(stream)))
+        int(nx), float(dx), float(w), float(rho_gj), int(open_bc), int(precision), int(n_elec),
+        ctypes.c_void_p(cell_e), ctypes.c_void_p(off_e), int(n_posi), ctypes.c_void_p(cell_p),
+        ctypes.c_void_p(off_p), ctypes.c_void_p(E), ctypes.byref(r), ctypes.c_void_p(stream)))
     return r.value
 
 

@@ -11,6 +11,8 @@ from scipy.integrate import quad
 from scipy.optimize import brentq
 from scipy.special import lambertw
 
+from paper_2012_05587_gb300 import analysis as _analysis
+
 
 # --- time-series measurements ------------------------------------------------
 
@@ -79,29 +81,10 @@ def relativistic_uniform_mode_period(E0: float, n0: float) -> float:
     return 4.0 * val
 
 
-def frozen_field_cascade_rate(E0, gamma_thr, eps_gamma, delay) -> float:
-    """Exact growth rate of the threshold cascade in a frozen uniform field.
-
-    In a uniform field u grows linearly, so a lepton at the threshold
-    (u_thr = sqrt(gamma_thr^2 - 1)) that recoils to gamma_thr - eps (u_r) emits
-    again after T1 = (u_thr - u_r) / E0.  Each photon becomes, after the flight
-    delay d, two leptons of gamma = eps / 2 (u_p) moving along it (Section 2):
-    the one whose charge the field accelerates forward reaches the threshold
-    after T2 = (u_thr - u_p) / E0, the other turns around and needs
-    T3 = (u_thr + u_p) / E0.  Counting descendants (Euler-Lotka) gives
-        exp(-G (T2 + d)) + exp(-G (T3 + d)) = 1 - exp(-G T1).
-    For f << 1 and d = 0 this reduces to Eq. 3."""
-    ut = np.sqrt(gamma_thr ** 2 - 1.0)
-    ur = np.sqrt((gamma_thr - eps_gamma) ** 2 - 1.0)
-    up = np.sqrt((eps_gamma / 2.0) ** 2 - 1.0)
-    T1 = (ut - ur) / E0
-    T2 = (ut - up) / E0
-    T3 = (ut + up) / E0
-
-    def fn(G):
-        return np.exp(-G * (T2 + delay)) + np.exp(-G * (T3 + delay)) - (1.0 - np.exp(-G * T1))
-
-    return brentq(fn, 1e-9 / T1, 50.0 / T1)
+# Exact growth rate of the threshold cascade in a frozen uniform field (the
+# renewal equation of the model's lepton generations; reduces to Eq. 3 for
+# f << 1): one copy, shared with the benchmark's reports.
+frozen_field_cascade_rate = _analysis.renewal_growth_rate
 
 
 def two_population_rate(E0, gamma_thr, eps_gamma, delay=0.0) -> float:
