@@ -49,7 +49,9 @@ typedef enum {
 } cascade_status;
 
 /* CASCADE_FP64: every particle and grid quantity in FP64.
- * CASCADE_FP32_MIXED: int32 cell + FP32 offset and momentum; the per-CTA
+ * CASCADE_FP32_MIXED: int32 cell + FP32 offset and momentum (one FP32 word,
+ *   or a compensated pair of two where one word cannot resolve the push at
+ *   the threshold; see u_words); the per-CTA
  *   current is accumulated in int32 fixed point at a scale chosen per launch
  *   so no sum can overflow (resolution 2^-10 or finer per contribution at the
  *   largest sizes), then summed over CTAs, applied to E and reduced for the
@@ -88,7 +90,12 @@ typedef struct {
                             equals the nearest edge, particles crossing x = 0 or x = L
                             deposit the path inside and are removed, photons that would
                             convert outside are not kept; 0: periodic */
-  int32_t reserved_;     /* set to 0 */
+  int32_t u_words;       /* FP32 modes: FP32 words per particle momentum.  0 = chosen at
+                            creation: two when one word cannot resolve a push at the
+                            threshold (cascade_momentum_words), else one; 1 = one
+                            word (rejected where two are needed); 2 = two words, a
+                            compensated hi + lo pair (4 B more per particle).
+                            Ignored in CASCADE_FP64. */
 } cascade_params;
 
 /* One record per step, taken after the step (time t = step dt).  Energies are
@@ -255,6 +262,15 @@ int cascade_batch_release(cascade_batch_t* b, int32_t slot);
 /* Number of slots, occupied slots and device bytes held by members. */
 int cascade_batch_info(cascade_batch_t* b, int32_t* slots, int32_t* occupied, size_t* bytes_in_use);
 
+/* Kernel timing of a batch, as cascade_set_timing / cascade_timing: with
+ * timing on, batch steps are launched directly (no graph replay) with a CUDA
+ * event pair around each launch of the batched particle kernel;
+ * cascade_batch_timing synchronises, returns the summed duration of those
+ * launches (ms), their number and the kernels launched, and clears them. */
+int cascade_batch_set_timing(cascade_batch_t* b, int32_t enable);
+int cascade_batch_timing(cascade_batch_t* b, double* particle_kernel_ms, int64_t* particle_kernel_launches,
+                         int64_t* kernels_launched);
+
 /* Release everything (NULL is accepted). */
 int cascade_batch_destroy(cascade_batch_t* b);
 
@@ -307,6 +323,21 @@ int cascade_destroy(cascade_t* h);
 /* Photon-flight steps n_pp = ceil(l_pp / dt - 1e-9) and device bytes a
  * cascade with these parameters allocates (for admission by footprint). */
 int cascade_footprint(const cascade_params* params, int32_t* n_pp_out, size_t* device_bytes_out);
+
+/* FP32 words per particle momentum that cascade_create would use for these
+ * parameters (1 or 2; 2 in CASCADE_FP64 stands for the FP64 word).  One FP32
+ * word suffices when half its spacing at the threshold momentum
+ * u_thr = sqrt(gamma_thr^2 - 1) is at most 2^-12 of the reference push
+ * F dt, F = |E0|, or gamma_thr / (nx dx) when E0 = 0 (the weakest uniform
+ * field that brings a lepton from rest to threshold across the domain).
+ * Otherwise the push of a lepton near threshold would lose more than 2^-12 of
+ * itself to rounding every step (at u = 7.3e7, the threshold Section 8
+ * estimates, the FP32 spacing is 8: any push below 4 is lost entirely), so
+ * the momentum is kept as a compensated pair of FP32 words whose sum carries
+ * about 48 bits.  CASCADE_ERR_INVALID_ARG for parameters outside the domain,
+ * or for u_words = 1 where two words are needed (the message names the
+ * limit). */
+int cascade_momentum_words(const cascade_params* params, int32_t* words_out);
 
 /* Human-readable text of a status code (static storage). */
 const char* cascade_status_string(int status);

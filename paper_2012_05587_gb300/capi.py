@@ -42,7 +42,7 @@ class cascade_params(ctypes.Structure):
         ("particle_cap", ctypes.c_int64), ("photon_cap", ctypes.c_int64),
         ("precision", ctypes.c_int32), ("diag_ring", ctypes.c_int32),
         ("j_m", ctypes.c_double), ("rho_gj", ctypes.c_double),
-        ("open_bc", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+        ("open_bc", ctypes.c_int32), ("u_words", ctypes.c_int32),
     ]
 
 
@@ -102,6 +102,7 @@ def load() -> ctypes.CDLL:
             "cascade_histogram": ([vp, i32, i32, i32, f64, f64, vp], ctypes.c_int),
             "cascade_destroy": ([vp], ctypes.c_int),
             "cascade_footprint": ([P(cascade_params), P(i32), P(ctypes.c_size_t)], ctypes.c_int),
+            "cascade_momentum_words": ([P(cascade_params), P(i32)], ctypes.c_int),
             "cascade_set_timing": ([vp, i32], ctypes.c_int),
             "cascade_timing": ([vp, P(f64), P(i64), P(i64)], ctypes.c_int),
             "cascade_gauss_noalloc": ([i32, f64, f64, f64, i32, i32, i64, vp, vp, i64, vp, vp, vp, P(f64), vp],
@@ -117,6 +118,8 @@ def load() -> ctypes.CDLL:
             "cascade_batch_release": ([vp, i32], ctypes.c_int),
             "cascade_batch_info": ([vp, P(i32), P(i32), P(ctypes.c_size_t)], ctypes.c_int),
             "cascade_batch_destroy": ([vp], ctypes.c_int),
+            "cascade_batch_set_timing": ([vp, i32], ctypes.c_int),
+            "cascade_batch_timing": ([vp, P(f64), P(i64), P(i64)], ctypes.c_int),
             "cascade_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "cascade_last_error_message": ([], ctypes.c_char_p),
         }
@@ -154,7 +157,7 @@ def make_params(p: dict) -> cascade_params:
         photon_cap=int(p.get("photon_cap", 0)), precision=int(prec),
         diag_ring=int(p.get("diag_ring", 0)),
         j_m=float(p.get("j_m", 0.0)), rho_gj=float(p.get("rho_gj", 0.0)),
-        open_bc=int(p.get("open_bc", 0)), reserved_=0,
+        open_bc=int(p.get("open_bc", 0)), u_words=int(p.get("u_words", 0)),
     )
 
 
@@ -310,6 +313,13 @@ def cascade_footprint(params: dict):
     return npp.value, b.value
 
 
+def cascade_momentum_words(params: dict) -> int:
+    w = ctypes.c_int32()
+    cp = make_params(params)
+    check("cascade_momentum_words", load().cascade_momentum_words(ctypes.byref(cp), ctypes.byref(w)))
+    return w.value
+
+
 # --- batches ---------------------------------------------------------------------------
 
 def _prec_code(prec) -> int:
@@ -388,6 +398,18 @@ def cascade_batch_info(b) -> dict:
     s, o, u = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
     check("cascade_batch_info", load().cascade_batch_info(b, ctypes.byref(s), ctypes.byref(o), ctypes.byref(u)))
     return {"slots": s.value, "occupied": o.value, "bytes": u.value}
+
+
+def cascade_batch_set_timing(b, enable: bool) -> None:
+    check("cascade_batch_set_timing", load().cascade_batch_set_timing(b, 1 if enable else 0))
+
+
+def cascade_batch_timing(b) -> dict:
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    k = ctypes.c_int64()
+    check("cascade_batch_timing", load().cascade_batch_timing(b, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)))
+    return {"particle_kernel_ms": ms.value, "particle_kernel_launches": n.value, "kernels_launched": k.value}
 
 
 def cascade_batch_destroy(b) -> None:

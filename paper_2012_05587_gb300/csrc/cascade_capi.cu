@@ -64,10 +64,38 @@ int validate(const cascade_params* p) {
   else if (p->diag_ring < 0) why = "diag_ring < 0";
   else if (p->open_bc != 0 && p->open_bc != 1) why = "open_bc must be 0 or 1";
   else if (!isfinite(p->j_m) || !isfinite(p->rho_gj)) why = "j_m and rho_gj must be finite";
+  else if (p->u_words < 0 || p->u_words > 2) why = "u_words must be 0, 1 or 2";
   if (why) {
     snprintf(g_msg, sizeof(g_msg), "invalid parameters: %s", why);
     return CASCADE_ERR_INVALID_ARG;
   }
+  return CASCADE_OK;
+}
+
+// FP32 words per particle momentum (see cascade_momentum_words in the
+// header): two when half the FP32 spacing at the threshold momentum exceeds
+// 2^-12 of the reference push F dt.  Returns CASCADE_ERR_INVALID_ARG when the
+// caller asks for one word where two are needed.
+int momentum_words(const cascade_params* p, int* words) {
+  if (p->precision == CASCADE_FP64) {
+    *words = 2;
+    return CASCADE_OK;
+  }
+  const double u_thr = sqrt(p->gamma_thr * p->gamma_thr - 1.0);
+  int e = 0;
+  frexp(u_thr, &e);                          // u_thr = m 2^e, m in [0.5, 1)
+  const double half_spacing = ldexp(1.0, e - 25);  // FP32 keeps 24 bits
+  const double F = p->E0 != 0.0 ? fabs(p->E0) : p->gamma_thr / ((double)p->nx * p->dx);
+  const double push = F * p->dt;
+  const bool two = half_spacing > ldexp(push, -12);
+  if (p->u_words == 1 && two) {
+    snprintf(g_msg, sizeof(g_msg),
+             "one FP32 word cannot resolve the momentum at threshold: half its spacing at u_thr = %.6g is %.3g, "
+             "above 2^-12 of the push %.3g per step (use u_words = 0 or 2)",
+             u_thr, half_spacing, push);
+    return CASCADE_ERR_INVALID_ARG;
+  }
+  *words = (p->u_words == 2 || two) ? 2 : 1;
   return CASCADE_OK;
 }
 
@@ -141,11 +169,15 @@ struct Plan {
   long long cap4, ph_cap;
   int n_pp, ring;
   size_t real;
+  size_t ulo;  // bytes of the low momentum word per particle (two-word FP32 momenta)
 };
 
 Plan plan_of(const cascade_params* p) {
   Plan pl;
   pl.real = p->precision == CASCADE_FP64 ? sizeof(double) : sizeof(float);
+  int words = 1;
+  momentum_words(p, &words);
+  pl.ulo = (p->precision != CASCADE_FP64 && words == 2) ? sizeof(float) : 0;
   pl.cap4 = (p->particle_cap + 3) & ~3LL;
   pl.ph_cap = next_pow2(p->photon_cap > 0 ? p->photon_cap : p->particle_cap);
   pl.n_pp = n_pp_of(p);
@@ -198,7 +230,16 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
   d.open_bc = params->open_bc;
   d.j_m = params->j_m;
   d.rho_gj = params->rho_gj;
+  int words = 1;
+  rc = momentum_words(params, &words);
+  if (rc) return rc;
+  d.u_words = params->precision == CASCADE_FP64 ? 1 : words;
   e = params->precision == CASCADE_FP64 ? configure_fp64(d, h->num_sms) : configure_fp32(d, h->num_sms);
+  if (e == cudaErrorNotSupported && d.u_words == 2) {
+    snprintf(g_msg, sizeof(g_msg),
+             "two-word FP32 momenta need the grid's current to fit shared memory (nx = %d)", params->nx);
+    return CASCADE_ERR_INVALID_ARG;
+  }
   if (e == cudaErrorInvalidValue && params->open_bc) {
     snprintf(g_msg, sizeof(g_msg), "open boundaries need the grid's E or current to fit shared memory (nx = %d)",
              params->nx);
@@ -213,6 +254,10 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
     d.off[s] = h->dalloc(R * pl.cap4);
     d.u[s] = h->dalloc(R * pl.cap4);
     if (!d.cell[s] || !d.off[s] || !d.u[s]) return CASCADE_ERR_OOM;
+    if (pl.ulo) {
+      d.ulo[s] = static_cast<float*>(h->dalloc(pl.ulo * pl.cap4));
+      if (!d.ulo[s]) return CASCADE_ERR_OOM;
+    }
   }
   d.ph_cell = static_cast<int32_t*>(h->dalloc(sizeof(int32_t) * pl.ph_cap));
   d.ph_off = h->dalloc(R * pl.ph_cap);
@@ -562,6 +607,10 @@ int cascade_particles(cascade_t* h, int32_t species, int64_t max, int32_t* cell,
     if (u) {
       CUDA_TRY(cudaMemcpy(tmp.data(), h->d.u[species], sizeof(float) * n, cudaMemcpyDeviceToHost));
       for (long long i = 0; i < n; ++i) u[i] = tmp[i];
+      if (h->d.ulo[species]) {  // two-word momenta: add the low word
+        CUDA_TRY(cudaMemcpy(tmp.data(), h->d.ulo[species], sizeof(float) * n, cudaMemcpyDeviceToHost));
+        for (long long i = 0; i < n; ++i) u[i] += (double)tmp[i];
+      }
     }
   }
   return h->sticky;
@@ -613,10 +662,12 @@ int cascade_footprint(const cascade_params* params, int32_t* n_pp_out, size_t* d
   g_msg[0] = '\0';  // a message describes this call only
   int rc = validate(params);
   if (rc) return rc;
+  int words = 1;
+  if ((rc = momentum_words(params, &words))) return rc;
   const Plan pl = plan_of(params);
   if (n_pp_out) *n_pp_out = pl.n_pp;
   if (device_bytes_out) {
-    size_t b = 2 * (sizeof(int32_t) + 2 * pl.real) * (size_t)pl.cap4;
+    size_t b = 2 * (sizeof(int32_t) + 2 * pl.real + pl.ulo) * (size_t)pl.cap4;
     b += (sizeof(int32_t) + pl.real) * (size_t)pl.ph_cap;
     b += sizeof(double) * (size_t)params->nx * 4;
     // per-CTA partials: at most 4 CTAs per SM on a 152-SM part
@@ -624,6 +675,17 @@ int cascade_footprint(const cascade_params* params, int32_t* n_pp_out, size_t* d
     b += sizeof(cascade_diag_t) * (size_t)pl.ring + 64 * 1024;
     *device_bytes_out = b;
   }
+  return CASCADE_OK;
+}
+
+int cascade_momentum_words(const cascade_params* params, int32_t* words_out) {
+  g_msg[0] = '\0';  // a message describes this call only
+  int rc = validate(params);
+  if (rc) return rc;
+  int words = 1;
+  rc = momentum_words(params, &words);
+  if (rc) return rc;
+  if (words_out) *words_out = words;
   return CASCADE_OK;
 }
 
@@ -696,10 +758,28 @@ struct cascade_batch {
   BatchDev bd{};
   int grid = 0, block = 0, dep = 0;
   size_t smem = 0;
+  // kernel timing (cascade_batch_set_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  long long kernels_launched = 0;
 
-  cudaError_t launch_step() const {
-    return precision == CASCADE_FP64 ? batch_step_fp64(bd, grid, block, smem, dep, stream)
-                                     : batch_step_fp32(bd, grid, block, smem, dep, stream);
+  cudaError_t launch_step() {
+    cudaEvent_t before = nullptr, after = nullptr;
+    if (timing) {
+      while (ev_pool.size() < ev_used + 2) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        ev_pool.push_back(e);
+      }
+      before = ev_pool[ev_used];
+      after = ev_pool[ev_used + 1];
+      ev_used += 2;
+      kernels_launched += 4;
+    }
+    return precision == CASCADE_FP64 ? batch_step_fp64(bd, grid, block, smem, dep, stream, before, after)
+                                     : batch_step_fp32(bd, grid, block, smem, dep, stream, before, after);
   }
 };
 
@@ -728,6 +808,9 @@ int batch_capture(cascade_batch_t* b) {
 // Queue nsteps batch steps and a snapshot of the remaining counts.
 int batch_enqueue(cascade_batch_t* b, int nsteps) {
   int left = nsteps;
+  if (b->timing) {  // every step launched directly, with events around the particle kernel
+    for (; left > 0; --left) CUDA_TRY(b->launch_step());
+  }
   if (left >= kGraphSteps && !b->graph) {
     int rc = batch_capture(b);
     if (rc) return rc;
@@ -755,6 +838,20 @@ int batch_member_check(cascade_batch_t* b, int slot) {
 }
 
 bool same_kernel_class(int a, int c) { return (a == CASCADE_FP64) == (c == CASCADE_FP64) && a == c; }
+
+// Batch members keep one-word FP32 momenta (the batched particle kernel has
+// no two-word form).
+int batch_member_words(const cascade_params* p) {
+  int words = 1;
+  int rc = momentum_words(p, &words);
+  if (rc) return rc;
+  if (p->precision != CASCADE_FP64 && words == 2) {
+    snprintf(g_msg, sizeof(g_msg),
+             "batch members keep one-word FP32 momenta; these parameters need two (run the cascade alone)");
+    return CASCADE_ERR_INVALID_ARG;
+  }
+  return CASCADE_OK;
+}
 
 }  // namespace
 
@@ -857,6 +954,7 @@ int cascade_batch_admit(cascade_batch_t* b, const cascade_params* params, int32_
     snprintf(g_msg, sizeof(g_msg), "batch members are periodic (open_bc = 0)");
     return CASCADE_ERR_INVALID_ARG;
   }
+  if ((rc = batch_member_words(params))) return rc;
   if (params->nx > b->max_nx) {
     snprintf(g_msg, sizeof(g_msg), "member nx = %d exceeds the batch's max_nx = %d", params->nx, b->max_nx);
     return CASCADE_ERR_INVALID_ARG;
@@ -921,6 +1019,12 @@ int cascade_batch_create(const cascade_params* params, int32_t n, size_t hbm_bud
     }
     if (params[i].open_bc) {
       snprintf(g_msg, sizeof(g_msg), "member %d: batch members are periodic (open_bc = 0)", i);
+      return CASCADE_ERR_INVALID_ARG;
+    }
+    if (batch_member_words(&params[i])) {
+      char why[sizeof(g_msg)];
+      snprintf(why, sizeof(why), "%s", g_msg);
+      snprintf(g_msg, sizeof(g_msg), "member %d: %s", i, why);
       return CASCADE_ERR_INVALID_ARG;
     }
     if (params[i].nx > max_nx) max_nx = params[i].nx;
@@ -1072,6 +1176,33 @@ int cascade_batch_info(cascade_batch_t* b, int32_t* slots, int32_t* occupied, si
   return CASCADE_OK;
 }
 
+int cascade_batch_set_timing(cascade_batch_t* b, int32_t enable) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!b) return CASCADE_ERR_INVALID_ARG;
+  b->timing = enable != 0;
+  return CASCADE_OK;
+}
+
+int cascade_batch_timing(cascade_batch_t* b, double* particle_kernel_ms, int64_t* particle_kernel_launches,
+                         int64_t* kernels_launched) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!b) return CASCADE_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < b->ev_used; i += 2) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, b->ev_pool[i], b->ev_pool[i + 1]));
+    total += ms;
+  }
+  if (particle_kernel_ms) *particle_kernel_ms = total;
+  if (particle_kernel_launches) *particle_kernel_launches = (int64_t)(b->ev_used / 2);
+  if (kernels_launched) *kernels_launched = b->kernels_launched;
+  b->ev_used = 0;
+  b->kernels_launched = 0;
+  return CASCADE_OK;
+}
+
 int cascade_batch_destroy(cascade_batch_t* b) {
   if (!b) return CASCADE_OK;
   cudaSetDevice(b->device);
@@ -1087,6 +1218,7 @@ int cascade_batch_destroy(cascade_batch_t* b) {
     if (b->h_snap[k]) cudaFreeHost(b->h_snap[k]);
   }
   if (b->ev_init) cudaEventDestroy(b->ev_init);
+  for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
   if (b->h_devs) cudaFreeHost(b->h_devs);
   if (b->h_set) cudaFreeHost(b->h_set);
   if (b->d_block) cudaFree(b->d_block);

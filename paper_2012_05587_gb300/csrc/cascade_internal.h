@@ -49,6 +49,7 @@ struct Dev {
   int32_t* cell[2];
   void* off[2];
   void* u[2];
+  float* ulo[2];       // FP32 two-word momentum: the low word (u = u + ulo), else null
   // photon ring: conversion cell (bit 31 = direction is -x) and offset
   int32_t* ph_cell;
   void* ph_off;
@@ -72,6 +73,7 @@ struct Dev {
   int push_fast;       // 1: gamma from one reciprocal square root (FP32 only)
   int push_stage;      // 1: particles staged through shared memory with cp.async (FP32)
   int fine_deposit;    // FP32: two-word accumulator (CASCADE_FP32_MIXED_FINE)
+  int u_words;         // FP32: 2 = momentum as a compensated pair (u, ulo), else 1
   int prefetch;        // particle kernel: iterations ahead to prefetch into L2 (0 = off)
   int open_bc;         // 1: open boundaries (co-rotating frame runs), 0: periodic
   double j_m;          // background current in Ampere's law
@@ -118,7 +120,8 @@ void set_error_message(const char* msg);
   cudaError_t batch_configure_##SUFFIX(int max_nx, int fine, int num_sms, int* grid, int* block,   \
                                        size_t* smem, int* dep);                                 \
   cudaError_t batch_step_##SUFFIX(const BatchDev& b, int grid, int block, size_t smem, int dep,   \
-                                  cudaStream_t s);                                              \
+                                  cudaStream_t s, cudaEvent_t before = nullptr,                 \
+                                  cudaEvent_t after = nullptr);                                 \
   size_t partial_bytes_##SUFFIX();                                                             \
   cudaError_t histogram_##SUFFIX(const Dev& d, int sp, int quantity, int nbins, double lo, double hi,    \
                                  unsigned long long* out, cudaStream_t s);                           \

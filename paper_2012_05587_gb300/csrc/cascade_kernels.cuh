@@ -101,8 +101,13 @@ __global__ void k_seed(Dev d, long long npairs, int ppc, unsigned long long seed
     d.cell[1][j] = cell;
     off0[j] = (Real)off;
     off1[j] = (Real)off;
-    u0[j] = (Real)(u_spread * ze);
-    u1[j] = (Real)(u_spread * zp);
+    const double ue = u_spread * ze, up = u_spread * zp;
+    u0[j] = (Real)ue;
+    u1[j] = (Real)up;
+    if (d.ulo[0]) {  // two-word momenta: the rounding residual
+      d.ulo[0][j] = (float)(ue - (double)(Real)ue);
+      d.ulo[1][j] = (float)(up - (double)(Real)up);
+    }
   }
 }
 
@@ -153,6 +158,11 @@ __global__ void k_convert(Dev d) {
     d.cell[1][n1 + i] = cell;
     off1[n1 + i] = oc;
     u1[n1 + i] = uv;
+    if (d.ulo[0]) {  // two-word momenta: the rounding residual of u_pair
+      const float lo = (float)(d.u_pair - (double)up);
+      d.ulo[0][n0 + i] = (enc < 0) ? -lo : lo;
+      d.ulo[1][n1 + i] = (enc < 0) ? -lo : lo;
+    }
   }
 }
 
@@ -280,9 +290,16 @@ __device__ __forceinline__ void set_scales(PushState<Real, DEP>& st, double pcou
 // STG: the four particles were already copied into this thread's shared
 // memory slots stg[0..2] (cell, offset, momentum; zero beyond cnt) by
 // cp.async; otherwise they are loaded from global memory here.
-template <class Real, int V, int DEP, bool FAST, bool OPEN, bool STG = false>
+// COMP (FP32 only): the momentum is a compensated pair of FP32 words, u + ulo
+// with |ulo| at most half the spacing of u.  The push adds q dt E to the pair
+// exactly up to the rounding of the low word (Knuth's TwoSum, written with
+// round-to-nearest intrinsics so that no operation is contracted), so pushes
+// far below the spacing of u still accumulate; the threshold test and the
+// recoil of a lepton near or above gamma_thr use the pair's sum in FP64.
+template <class Real, int V, int DEP, bool FAST, bool OPEN, bool STG = false, bool COMP = false>
 __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP>& st, int s, long long base,
                                          int cnt, int lane, const unsigned char* const* stg = nullptr) {
+  static_assert(!COMP || (sizeof(Real) == 4 && !STG), "two-word momenta: FP32, direct loads");
   typedef typename AccOf<Real, DEP>::type Acc;
   const int nx = d.nx;
   const Real dt = (Real)d.dt, dtdx = (Real)d.dtdx;
@@ -293,6 +310,17 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
   Real* up = static_cast<Real*>(d.u[s]) + base;
   int cl[4] = {0, 0, 0, 0};
   Real of[4] = {zero, zero, zero, zero}, uu[4] = {zero, zero, zero, zero};
+  float ul[4] = {0.f, 0.f, 0.f, 0.f};
+  float* ulp = COMP ? d.ulo[s] + base : nullptr;
+  if (COMP) {
+    if (cnt == 4) {
+      ld4(ulp, ul);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < cnt) ul[j] = ulp[j];
+    }
+  }
   if (STG) {
     if (cnt > 0) {
       ld4(reinterpret_cast<const int*>(stg[0]), cl);
@@ -357,7 +385,21 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
   for (int j = 0; j < 4; ++j) {
     const int c = cl[j];
     const Real o = of[j];
-    const Real u = uu[j] + qdt * Ep[j];
+    Real u;
+    if constexpr (COMP) {
+      // (uu, ul) + du as a new pair: TwoSum of the high words, the error and
+      // the low word added, then renormalised (Fast2Sum)
+      const float du = __fmul_rn((float)qdt, (float)Ep[j]);
+      const float sh = __fadd_rn((float)uu[j], du);
+      const float bv = __fsub_rn(sh, (float)uu[j]);
+      const float er = __fadd_rn(__fsub_rn((float)uu[j], __fsub_rn(sh, bv)), __fsub_rn(du, bv));
+      const float lo = __fadd_rn(ul[j], er);
+      const float hi = __fadd_rn(sh, lo);
+      ul[j] = __fsub_rn(lo, __fsub_rn(hi, sh));
+      u = (Real)hi;
+    } else {
+      u = uu[j] + qdt * Ep[j];
+    }
     Real gj, dd;
     Kin<Real, FAST>::eval(u, dtdx, gj, dd);
     Real o2 = o + dd;
@@ -476,7 +518,10 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
     }
   }
 
-  const bool hot = (g[0] >= thr) | (g[1] >= thr) | (g[2] >= thr) | (g[3] >= thr) |
+  // two-word momenta: the FP32 gamma only preselects (its rounding is far
+  // below 2^-20 relative); the FP64 test below decides
+  const Real thr_pre = COMP ? thr * Real(0.999999) : thr;
+  const bool hot = (g[0] >= thr_pre) | (g[1] >= thr_pre) | (g[2] >= thr_pre) | (g[3] >= thr_pre) |
                    !(g[0] <= Real(1e30)) | !(g[1] <= Real(1e30)) | !(g[2] <= Real(1e30)) |
                    !(g[3] <= Real(1e30));
   if (__any_sync(kFull, hot)) {
@@ -492,15 +537,18 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
         // non-finite or absurd gamma: the run has blown up; flag it, no emission
         set_error(st.ctl, CASCADE_ERR_NONFINITE);
         emit = false;
-      } else if (sizeof(Real) == 4 && gj > Real(1e6)) {
-        // large gamma: threshold test and recoil in FP64
-        const double ud = (double)u;
+      } else if (COMP || (sizeof(Real) == 4 && gj > Real(1e6))) {
+        // large gamma, or a two-word momentum: threshold test and recoil in
+        // FP64 (of the pair's sum for a two-word momentum)
+        const double ud = (double)u + (double)ul[j];
         const double gd = sqrt(1.0 + ud * ud);
         emit = gd >= d.gamma_thr;
         if (emit) {
           k = 1 + (int)fmin(floor((gd - d.gamma_thr) / d.eps_gamma), (double)kMaxPhotonsPerStep);
           const double g2 = gd - (double)k * d.eps_gamma;
-          u = (Real)((fwd ? 1.0 : -1.0) * sqrt(g2 * g2 - 1.0));
+          const double un = (fwd ? 1.0 : -1.0) * sqrt(g2 * g2 - 1.0);
+          u = (Real)un;
+          if (COMP) ul[j] = (float)(un - (double)u);
           gj = (Real)g2;
         }
       } else {
@@ -582,6 +630,7 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
     st4(cellp, cl);
     st4(offp, of);
     st4(up, uu);
+    if (COMP) st4(ulp, ul);
   } else {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -589,6 +638,7 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
         cellp[j] = cl[j];
         offp[j] = of[j];
         up[j] = uu[j];
+        if (COMP) ulp[j] = ul[j];
       }
     }
   }
@@ -627,7 +677,8 @@ constexpr size_t kStageBytesPerThread = 2 * 3 * 16;
 // STG (FP32 only): the particles of the next iteration are copied into
 // shared memory with cp.async while the current ones are processed, so each
 // thread keeps one iteration of loads in flight at all times.
-template <class Real, int V, int DEP, bool FAST, bool OPEN, bool STG = false>
+// COMP: two-word momenta (see process4); direct loads.
+template <class Real, int V, int DEP, bool FAST, bool OPEN, bool STG = false, bool COMP = false>
 __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
   static_assert(!STG || sizeof(Real) == 4, "the staging slots hold four 4-byte values");
   typedef typename AccOf<Real, DEP>::type Acc;
@@ -704,6 +755,7 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
           prefetch_l2(d.cell[sp] + bp, (unsigned)(np * 4) & ~15u);
           prefetch_l2(static_cast<const Real*>(d.off[sp]) + bp, (unsigned)(np * sizeof(Real)) & ~15u);
           prefetch_l2(static_cast<const Real*>(d.u[sp]) + bp, (unsigned)(np * sizeof(Real)) & ~15u);
+          if (COMP) prefetch_l2(d.ulo[sp] + bp, (unsigned)(np * 4) & ~15u);
         }
       }
     }
@@ -723,7 +775,7 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
       const unsigned char* stg[3] = {slot(b, 0), slot(b, 1), slot(b, 2)};
       gsum_total += (double)process4<Real, V, DEP, FAST, OPEN, true>(d, st, s, base, cnt, lane, stg);
     } else {
-      gsum_total += (double)process4<Real, V, DEP, FAST, OPEN>(d, st, s, base, cnt, lane);
+      gsum_total += (double)process4<Real, V, DEP, FAST, OPEN, false, COMP>(d, st, s, base, cnt, lane);
     }
   }
 
@@ -1017,6 +1069,7 @@ __global__ void k_compact_move(Dev d) {
       d.cell[s][to] = d.cell[s][from];
       off[to] = off[from];
       u[to] = u[from];
+      if (d.ulo[s]) d.ulo[s][to] = d.ulo[s][from];
     }
   }
 }
@@ -1071,6 +1124,11 @@ __global__ void k_batch_convert(BatchDev b) {
     d.cell[1][n1 + i] = cell;
     off1[n1 + i] = oc;
     u1[n1 + i] = uv;
+    if (d.ulo[0]) {  // two-word momenta: the rounding residual of u_pair
+      const float lo = (float)(d.u_pair - (double)up);
+      d.ulo[0][n0 + i] = (enc < 0) ? -lo : lo;
+      d.ulo[1][n1 + i] = (enc < 0) ? -lo : lo;
+    }
   }
 }
 
@@ -1350,7 +1408,9 @@ __global__ void k_upload(Dev d, int s, long long first, long long count, const d
     Real oo = (Real)o;
     if (!(oo < Real(1))) oo = Real(1) - (sizeof(Real) == 4 ? Real(5.9604645e-8) : Real(1.1102230246251565e-16));
     off[i] = ok ? oo : Real(0);
-    u[i] = ok ? (Real)uu : Real(0);
+    const Real uh = ok ? (Real)uu : Real(0);
+    u[i] = uh;
+    if (d.ulo[s]) d.ulo[s][first + i] = ok ? (float)(uu - (double)uh) : 0.f;  // two-word momenta
     nbad += ok ? 0u : 1u;
   }
   if (nbad) atomicAdd(bad, nbad);
@@ -1374,8 +1434,9 @@ __global__ void k_histogram(Dev d, int s, int quantity, int nbins, double lo, do
        p += (long long)gridDim.x * blockDim.x) {
     if (d.cell[s][p] < 0) continue;  // departed (open boundaries)
     double v;
-    if (quantity == 0) v = (double)u[p];
-    else if (quantity == 1) v = sqrt(1.0 + (double)u[p] * (double)u[p]);
+    const double up = (double)u[p] + (d.ulo[s] ? (double)d.ulo[s][p] : 0.0);
+    if (quantity == 0) v = up;
+    else if (quantity == 1) v = sqrt(1.0 + up * up);
     else v = ((double)d.cell[s][p] + (double)off[p]) * d.dx;
     if (v >= lo && v < hi) {
       int b = (int)((v - lo) * scale);
@@ -1437,10 +1498,10 @@ __global__ void k_gauss_reduce(Dev d, const double* rho_dx, double* out) {
 // accumulator.
 template <class Real>
 struct PushTable {
-  static const void* get(int V, int dep, bool fast, bool open, bool stage);
+  static const void* get(int V, int dep, bool fast, bool open, bool stage, bool comp = false);
 };
 template <>
-inline const void* PushTable<double>::get(int V, int, bool, bool open, bool) {
+inline const void* PushTable<double>::get(int V, int, bool, bool open, bool, bool) {
   if (V == kSmemESmemS)
     return open ? reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false, true>)
                 : reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false, false>);
@@ -1451,7 +1512,19 @@ inline const void* PushTable<double>::get(int V, int, bool, bool open, bool) {
   return reinterpret_cast<const void*>(&k_push<double, kGlobEGlobS, 0, false, false>);
 }
 template <>
-inline const void* PushTable<float>::get(int V, int dep, bool, bool open, bool stage) {
+inline const void* PushTable<float>::get(int V, int dep, bool, bool open, bool stage, bool comp) {
+  if (comp) {  // two-word momenta: the shared-memory accumulator forms, direct loads
+    if (V == kSmemESmemS) {
+      if (open) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, true, false, true>);
+      if (dep == 4) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 4, true, false, false, true>);
+      return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, false, false, true>);
+    }
+    if (V == kGlobESmemS) {
+      if (open) return reinterpret_cast<const void*>(&k_push<float, kGlobESmemS, 1, true, true, false, true>);
+      return reinterpret_cast<const void*>(&k_push<float, kGlobESmemS, 1, true, false, false, true>);
+    }
+    return nullptr;
+  }
   if (V == kSmemESmemS) {
     if (stage && !open && dep == 1)
       return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, false, true>);
@@ -1482,7 +1555,8 @@ struct Launchers {
   }
 
   static const void* push_fn(const Dev& d) {
-    return PushTable<Real>::get(d.variant, d.push_dep, d.push_fast != 0, d.open_bc != 0, d.push_stage != 0);
+    return PushTable<Real>::get(d.variant, d.push_dep, d.push_fast != 0, d.open_bc != 0, d.push_stage != 0,
+                                sizeof(Real) == 4 && d.u_words == 2);
   }
 
   static cudaError_t configure(Dev& d, int num_sms) {
@@ -1509,6 +1583,12 @@ struct Launchers {
       variant = kSmemEGlobS;
     }
     if (variant == kGlobEGlobS) dep = 0;
+    const bool comp = sizeof(Real) == 4 && d.u_words == 2;
+    if (comp) {
+      // two-word momenta are built for the shared-memory accumulator forms
+      if (variant != kSmemESmemS && variant != kGlobESmemS) return cudaErrorNotSupported;
+      if (variant == kGlobESmemS && dep == 4) dep = 1;
+    }
     if (d.open_bc) {
       // open boundaries are built for the shared-memory accumulator variants
       // (plus E in shared memory with global FP64 atomics in FP64)
@@ -1522,7 +1602,7 @@ struct Launchers {
     const int block = PushBlock<Real>::value;
     d.block_push = block;
     d.push_stage = 0;
-    if (sizeof(Real) == 4 && variant == kSmemESmemS && dep == 1 && !d.open_bc &&
+    if (sizeof(Real) == 4 && variant == kSmemESmemS && dep == 1 && !d.open_bc && !comp &&
         env_int("CASCADE_PUSH_STAGE", 1) == 1) {
       // the staging area must fit beside E, the accumulator and the
       // kernel's static shared memory
@@ -1665,14 +1745,19 @@ struct Launchers {
     return cudaSuccess;
   }
 
-  static cudaError_t batch_step(const BatchDev& b, int grid, int block, size_t smem, int dep, cudaStream_t st) {
+  // One batch step; with events given, they are recorded around the
+  // particle kernel.
+  static cudaError_t batch_step(const BatchDev& b, int grid, int block, size_t smem, int dep, cudaStream_t st,
+                                cudaEvent_t before = nullptr, cudaEvent_t after = nullptr) {
     k_batch_convert<Real><<<dim3(16, b.n), 256, 0, st>>>(b);
     k_batch_plan<Real><<<1, 1024, 0, st>>>(b);
+    if (before) cudaEventRecord(before, st);
     BatchDev arg = b;
     void* args[] = {&arg};
     cudaError_t e = cudaLaunchKernel(batch_push_fn(dep % 16, (dep / 16) % 4, dep / 64 != 0), dim3(grid), dim3(block),
                                      args, smem, st);
     if (e != cudaSuccess) return e;
+    if (after) cudaEventRecord(after, st);
     k_batch_field<Real><<<b.n, kFieldBlock, 0, st>>>(b);
     return cudaGetLastError();
   }
@@ -1728,8 +1813,8 @@ struct Launchers {
     return Launchers<REAL>::batch_configure(max_nx, fine, num_sms, grid, block, smem, dep);       \
   }                                                                                               \
   cudaError_t batch_step_##SUFFIX(const BatchDev& b, int grid, int block, size_t smem, int dep,   \
-                                  cudaStream_t s) {                                               \
-    return Launchers<REAL>::batch_step(b, grid, block, smem, dep, s);                             \
+                                  cudaStream_t s, cudaEvent_t before, cudaEvent_t after) {        \
+    return Launchers<REAL>::batch_step(b, grid, block, smem, dep, s, before, after);              \
   }                                                                                               \
   size_t partial_bytes_##SUFFIX() { return sizeof(REAL); }                                       \
   cudaError_t histogram_##SUFFIX(const Dev& d, int sp, int q, int nb, double lo, double hi,          \

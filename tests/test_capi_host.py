@@ -125,3 +125,38 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(capi, "LIB_PATH", str(tmp_path / "libcascade.so"))
     with pytest.raises(ImportError, match="missing"):
         capi.load()
+
+
+def test_momentum_words_rule():
+    """One FP32 word suffices where half its spacing at the threshold momentum
+    is at most 2^-12 of the push per step; otherwise two words are used, and
+    asking for one is rejected with a message naming the limit."""
+    assert capi.cascade_momentum_words(W.large_cascade()) == 1            # u_thr = 50, push 2.5
+    assert capi.cascade_momentum_words(W.small_cascade(precision="fp32")) == 1
+    for p in W.precision_sweep() + W.batch_scan(64):
+        assert capi.cascade_momentum_words(p) == 1
+    # Section 8's threshold, gamma_thr ~ 7.3e7: FP32 spacing 8 against a push of 8
+    hot = dict(W.small_cascade(precision="fp32"), E0=1024.0, dt=1.0 / 128.0, gamma_thr=7.3e7, eps_gamma=7.3e5)
+    assert capi.cascade_momentum_words(hot) == 2
+    with pytest.raises(capi.CascadeError) as ei:
+        capi.cascade_momentum_words(dict(hot, u_words=1))
+    assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG and "2^-12" in str(ei.value)
+    # no initial field: the reference push uses gamma_thr / L (co-rotating frame)
+    assert capi.cascade_momentum_words(W.corotating()) == 2
+    # forcing two words is always allowed; the footprint grows by 4 B per particle and species
+    small = W.small_cascade(precision="fp32")
+    assert capi.cascade_momentum_words(dict(small, u_words=2)) == 2
+    _, b1 = capi.cascade_footprint(small)
+    _, b2 = capi.cascade_footprint(dict(small, u_words=2))
+    cap4 = (small["particle_cap"] + 3) // 4 * 4
+    assert b2 - b1 == 2 * 4 * cap4
+    with pytest.raises(capi.CascadeError):
+        capi.cascade_momentum_words(dict(small, u_words=3))
+
+
+def test_batch_rejects_two_word_members():
+    ps = [W.small_cascade(precision="fp32"), dict(W.small_cascade(precision="fp32"), u_words=2)]
+    with pytest.raises(capi.CascadeError) as ei:
+        capi.cascade_batch_create(ps, 0, 0)
+    assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
+    assert "member 1: batch members keep one-word FP32 momenta" in str(ei.value)

@@ -241,9 +241,11 @@ def test_staged_particle_stream_matches_direct_loads(monkeypatch):
     staging in shared memory (the default where it fits) or with direct loads.
     Without emission (gamma_thr out of reach) both give bit-identical fields
     and particles; 2 x 1,032,129 particles on Nx = 16383 span several
-    iterations per CTA and end in a ragged chunk."""
-    p = dict(W.large_cascade(precision="fp32"), nx=16383, ppc=63, gamma_thr=1e9, eps_gamma=20.0,
+    iterations per CTA and end in a ragged chunk.  (gamma_thr = 1e4 is out of
+    reach in 50 steps and keeps the one-word momentum that staging serves.)"""
+    p = dict(W.large_cascade(precision="fp32"), nx=16383, ppc=63, gamma_thr=1e4, eps_gamma=20.0,
              particle_cap=1 << 21, u_spread=0.3)
+    assert capi.cascade_momentum_words(p) == 1
     out = {}
     for stage in ("1", "0"):
         monkeypatch.setenv("CASCADE_PUSH_STAGE", stage)
