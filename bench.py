@@ -15,6 +15,10 @@ e2e        the same metric through the C ABI with host buffers: the state is
 roofline   the particle kernel against the measured HBM copy bandwidth:
            24 algorithmic bytes per particle-step (int32 cell + FP32 offset +
            FP32 momentum, read and written)
+qed_active the same metric and roofline on two timed phases in which the
+           QED model works: the cascade itself (steps 0-200, the particle
+           count growing from the seed to screening) and the secondary pair
+           bursts that damp the oscillation (from step 1000)
 cpu_baseline  the FP64 oracle on a bounded slice of the same workload
 
 ``--impl reference`` times the oracle (the only reference this method has)
@@ -65,11 +69,17 @@ def parse():
     ap.add_argument("--prep", type=int, default=400, help="untimed steps that grow the cascade")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--cascade-steps", type=int, default=200,
+                    help="large workload: first steps timed as the cascade phase (0 = skip)")
+    ap.add_argument("--burst-start", type=int, default=1000,
+                    help="large workload: step where the timed secondary-burst phase starts (0 = skip)")
+    ap.add_argument("--burst-steps", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cap", type=int, default=0, help="particle cap per species (0 = the workload's)")
     ap.add_argument("--ppc", type=int, default=0, help="seed particles per cell per species (0 = the workload's)")
-    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "sweep", "paper", "corotating"],
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "batch", "serve", "sweep", "paper", "corotating", "damping"],
                     help="large: one large cascade (default); batch: the 256-cascade parameter scan in one "
                          "launch per step; serve: Poisson arrivals admitted by footprint; sweep: FP32 vs FP64 "
                          "errors of the ensemble diagnostics")
@@ -77,11 +87,17 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3000)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=50.0)
-    ap.add_argument("--fp64-sample", type=int, default=8, help="cascades run one at a time in FP64 for comparison")
+    ap.add_argument("--serve-low-frac", type=float, default=0.5,
+                    help="serve workload: second run at this fraction of the measured capacity (0 = skip)")
+    ap.add_argument("--serve-low-requests", type=int, default=400)
+    ap.add_argument("--fp64-sample", type=int, default=32,
+                    help="cascades run one at a time in FP64 for comparison, spread evenly over the predicted "
+                         "particle-steps (0 = every scan member, or 64 requests when serving)")
     ap.add_argument("--paper-time", type=float, default=12.0, help="paper workload: simulated time (1/omega_p)")
     ap.add_argument("--save-series", default="", help="paper/corotating workloads: directory for the series")
     ap.add_argument("--corot-time", type=float, default=200.0, help="corotating workload: simulated time")
     ap.add_argument("--sweep-seeds", type=int, default=8, help="sweep workload: seeds averaged per configuration")
+    ap.add_argument("--damping-seeds", type=int, default=32, help="damping workload: seeds per precision")
     ap.add_argument("--sweep-rows", default="", help="sweep workload: comma-separated configuration indices (all)")
     return ap.parse_args()
 
@@ -281,7 +297,7 @@ def main():
     prec = args.precision
     p = W.large_cascade(run=rank, precision=prec)
     if prec == "fp64":
-        p["particle_cap"] = 150_000_000
+        p["particle_cap"] = 200_000_000  # 3.1e8 particles by step 1200, 20 B each
     if args.cap:
         p["particle_cap"] = args.cap
     if args.ppc:
@@ -293,8 +309,16 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    peak, peak_kind = measured_peak()
+    bpp = BYTES_PER_PARTICLE_STEP[prec]
     c = Cascade(p)
-    c.step(args.prep)
+    # the cascade phase, with emission and pair creation at every step
+    casc = None
+    if args.cascade_steps > 0:
+        casc = timed_phase(c, min(args.cascade_steps, args.prep), stream, bpp, peak, prec)
+        casc["what"] = (f"steps 0-{casc['steps']}: the pair cascade, from the seed to screening "
+                        "(emission, photon flight and pair creation active)")
+    c.step(args.prep - (casc["steps"] if casc else 0))
     c.step(args.warmup)
     c.sync()
     capi.cascade_set_timing(c.h, True)
@@ -322,8 +346,6 @@ def main():
     t_max, ps_all = aggregate_over_ranks(ms, ps, "cuda")
     value = ps_all / (t_max / 1e3)
 
-    peak, peak_kind = measured_peak()
-    bpp = BYTES_PER_PARTICLE_STEP[prec]
     avg_push_s = tim["particle_kernel_ms"] / 1e3 / max(tim["particle_kernel_launches"], 1)
     achieved = bpp * ps / args.steps / avg_push_s / 1e9
     tb = MEASURED_DRAM_BYTES_PER_PARTICLE_STEP.get(prec)
@@ -344,6 +366,15 @@ def main():
                 "peak_source": "152 SMs x 1 FP64 warp instruction per 16 cycles x sampled SM clock",
                 "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "bytes_per_particle_step": bpp}}
+
+    # the secondary pair bursts that damp the oscillation (Section 6)
+    burst = None
+    done = args.prep + args.warmup + args.steps
+    if args.burst_start > 0 and args.burst_steps > 0 and args.burst_start >= done:
+        c.step(args.burst_start - done)
+        burst = timed_phase(c, args.burst_steps, stream, bpp, peak, prec)
+        burst["what"] = (f"steps {args.burst_start}-{args.burst_start + args.burst_steps}: secondary pair bursts "
+                         "of the damping phase")
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -377,6 +408,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (particle state >> 129 MB)"},
             "roofline": roof,
+            "qed_active": {"cascade_phase": casc, "burst_phase": burst},
             "cpu_baseline": cpu,
             "cpu_multicore": cpu_mc,
             "e2e": e2e,
@@ -387,6 +419,46 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def timed_phase(c, nsteps, stream, bpp, peak, prec):
+    """nsteps steps of a cascade timed on its stream (CUDA events around the
+    whole steps and around every particle-kernel launch), with the QED
+    activity they contained.  The particle kernel's algorithmic bytes are
+    bpp per particle-step plus the photon entries it appends (cell and
+    offset: 8 B in FP32, 12 B in FP64)."""
+    import torch
+
+    from paper_2012_05587_gb300 import capi
+
+    c.sync()
+    capi.cascade_set_timing(c.h, True)
+    capi.cascade_timing(c.h)  # clear
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    c.step(nsteps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    tim = capi.cascade_timing(c.h)
+    capi.cascade_set_timing(c.h, False)
+    rec = c.diag(nsteps)
+    ps = float((rec["n_elec"] + rec["n_posi"]).sum())
+    pairs = float(rec["n_pairs_total"][-1] - rec["n_pairs_total"][0])
+    # photons emitted = photons in flight added + photons converted
+    photons = float(rec["n_photon"][-1] - rec["n_photon"][0]) + pairs
+    ph_bytes = 8 if prec == "fp32" else 12
+    push_s = tim["particle_kernel_ms"] / 1e3
+    achieved = (bpp * ps + ph_bytes * photons) / push_s / 1e9 if push_s > 0 else None
+    return {"steps": nsteps, "value": ps / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "particles_first": int(rec["n_elec"][0] + rec["n_posi"][0]),
+            "particles_last": int(rec["n_elec"][-1] + rec["n_posi"][-1]),
+            "pairs_created_per_particle_step": pairs / ps, "photons_emitted_per_particle_step": photons / ps,
+            "particle_kernel_share": push_s * 1e3 / ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None,
+                         "bytes": f"{bpp} B per particle-step + {ph_bytes} B per photon appended"}}
 
 
 def e2e_run(c, p, steps, stream, barrier):
@@ -404,12 +476,14 @@ def e2e_run(c, p, steps, stream, barrier):
     def pinned(shape, dtype):
         return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
 
+    # FP32 cascades take FP32 host arrays (12 B per particle); FP64 ones FP64 (20 B)
+    real = torch.float32 if p.get("precision", "fp32") != "fp64" else torch.float64
     host = {}
     for s, n in ((0, ne), (1, npo)):
         part = c.particles(s)
         hc = pinned(n, torch.int32)
-        ho = pinned(n, torch.float64)
-        hu = pinned(n, torch.float64)
+        ho = pinned(n, real)
+        hu = pinned(n, real)
         hc[:] = part["cell"]
         ho[:] = part["off"]
         hu[:] = part["u"]
@@ -434,8 +508,9 @@ def e2e_run(c, p, steps, stream, barrier):
     d2h = 112 * steps + E2.nbytes + J2.nbytes
     return {"value": ps / el, "unit": UNIT, "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
             "seconds": el, "create_and_upload_s": t_up, "steps_and_reads_s": el - t_up,
-            "what": "cascade_create_from_state from pinned host arrays + per step cascade_step(1) and "
-                    "cascade_diag(1) to host + final E/J to host; wall clock"}
+            "what": "cascade_create_from_state(_f32) from pinned host arrays (int32 cell, offset and momentum in "
+                    "the cascade's precision) + per step cascade_step(1) and cascade_diag(1) to host + final E/J "
+                    "to host; wall clock"}
 
 
 if __name__ == "__main__":

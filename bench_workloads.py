@@ -45,6 +45,22 @@ def _fp64_one_at_a_time(params: list, steps_of) -> dict:
             "per_request_s": times}
 
 
+def stratified(params: list, n: int, key) -> list:
+    """n members spread evenly over ``params`` sorted by ``key`` (every size
+    class represented); all of them when n <= 0 or n >= len(params)."""
+    if n <= 0 or n >= len(params):
+        return list(params)
+    order = sorted(range(len(params)), key=lambda i: key(params[i]))
+    return [params[order[int((k + 0.5) * len(params) / n)]] for k in range(n)]
+
+
+def _sample_note(n_sample: int, n_all: int, what: str) -> str:
+    if n_sample >= n_all:
+        return f"all {n_all} {what}, each alone in FP64"
+    return (f"{n_sample} of {n_all} {what}, spread evenly over the predicted particle-steps "
+            "(stratified), each alone in FP64")
+
+
 def run_batch(args) -> int:
     import torch
 
@@ -70,6 +86,8 @@ def run_batch(args) -> int:
     wall = time.perf_counter() - w0
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
+    variant = b.variant()
+    tuning = b.tuning_report()
     ps = 0.0
     over = 0
     pairs = photons = 0
@@ -84,7 +102,9 @@ def run_batch(args) -> int:
         photons += int(d["n_pairs_total"][-1] + d["n_photon"][-1])
     b.close()
     value = ps / (ms / 1e3)
-    fp64 = _fp64_one_at_a_time(scan[: args.fp64_sample], lambda p: args.batch_steps)
+    roof = _batch_roofline(scan, args.batch_steps, prec)
+    sample = stratified(scan, args.fp64_sample, lambda p: W.predicted_particles(p))
+    fp64 = _fp64_one_at_a_time(sample, lambda p: args.batch_steps)
     line = {
         "metric": B.METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.batch_steps, "warmup": 0,
         "ms_per_step": ms / args.batch_steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -97,36 +117,73 @@ def run_batch(args) -> int:
                    "pairs_created_per_particle_step": pairs / ps if ps else None,
                    "photons_emitted_per_particle_step": photons / ps if ps else None},
         "fp64_one_at_a_time": dict(fp64, per_request_s=None,
-                                   sample=f"first {args.fp64_sample} cascades of the scan, each alone in FP64"),
+                                   sample=_sample_note(len(sample), len(scan), "cascades of the scan")),
         "batched_over_fp64_one_at_a_time": value / fp64["value"] if fp64["value"] else None,
+        "roofline": roof,
+        "variant": variant,
+        "tuning": tuning,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serve(args) -> int:
+def _batch_roofline(scan: list, steps: int, prec: str) -> dict:
+    """The same scan again, launched step by step with CUDA events around
+    every launch of the batched particle kernel: its algorithmic traffic
+    (24 B per particle-step in FP32, 40 B in FP64) over its summed duration,
+    against the measured HBM copy bandwidth."""
     import torch
 
-    from paper_2012_05587_gb300 import CascadeBatch, CascadeError, workloads as W
+    from paper_2012_05587_gb300 import CascadeBatch, capi
 
-    prec = args.precision
-    reqs = W.serving_requests(args.requests, rate=args.rate, precision=prec)
-    free = torch.cuda.mem_get_info()[0]
-    budget = int(0.6 * free)
-    # a private stream: host reads of finished requests never wait for the batch
-    serve_stream = torch.cuda.Stream()
-    torch.cuda.set_stream(serve_stream)
+    peak, peak_kind = B.measured_peak()
+    bpp = B.BYTES_PER_PARTICLE_STEP["fp64" if prec == "fp64" else "fp32"]
+    b = CascadeBatch(scan)
+    capi.cascade_batch_set_timing(b.b, True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    b.step([steps] * len(scan))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    tim = capi.cascade_batch_timing(b.b)
+    ps = 0.0
+    for i in range(len(scan)):
+        try:
+            ps += _psteps(b.diag(i, steps))
+        except Exception:
+            continue
+    b.close()
+    push_s = tim["particle_kernel_ms"] / 1e3
+    achieved = bpp * ps / push_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_batch_push (gather/push/move/deposit/emission of every member)",
+            "bytes_per_particle_step": bpp, "peak_source": peak_kind,
+            "particle_kernel_share": push_s * 1e3 / ms, "launches": tim["particle_kernel_launches"],
+            "value_with_direct_launches": ps / (ms / 1e3)}
+
+
+def _serve(reqs: list, prec: str, budget: int) -> dict:
+    """Serve ``reqs`` (each with an arrival time) by continuous batching:
+    requests are admitted into free slots while their predicted device
+    footprint fits the budget, every loop runs 16 batch steps, and finished
+    requests are read back and released.  Returns the particle-steps served,
+    the wall time and each request's (arrival, admission, result) times."""
+    import torch
+
+    from paper_2012_05587_gb300 import CascadeBatch, CascadeError
+
     b = CascadeBatch(slots=256, precision=prec, max_nx=8192, hbm_budget=budget)
     pending = list(reqs)
     queue = []
     slot_req = {}
-    done = {}
+    done = []
     ps = 0.0
-    t0 = time.perf_counter()
-    sampler = B.ClockSampler(torch.cuda.current_device())
-    sampler.start()
     busy_rejects = 0
+    t0 = time.perf_counter()
     while len(done) < len(reqs):
         now = time.perf_counter() - t0
         while pending and pending[0]["arrival"] <= now:
@@ -154,27 +211,67 @@ def run_serve(args) -> int:
             rec = b.diag(slot, r["steps"])
             t_done = time.perf_counter() - t0
             ps += _psteps(rec)
-            done[id(r)] = (r["arrival"], t_adm, t_done)
+            done.append((r["arrival"], t_adm, t_done))
             b.release(slot)
     wall = time.perf_counter() - t0
-    clocks = sampler.stop()
     b.close()
-    ttr = np.array([d - a for a, _, d in done.values()])
-    fp64 = _fp64_one_at_a_time(reqs[: args.fp64_sample], lambda p: p["steps"])
+    torch.cuda.synchronize()
+    ttr = np.array([d - a for a, _, d in done])
+    wait = np.array([m - a for a, m, _ in done])
+    return {"particle_steps": ps, "wall_s": wall, "value": ps / wall, "requests": len(reqs),
+            "p50_time_to_result_s": float(np.percentile(ttr, 50)),
+            "p99_time_to_result_s": float(np.percentile(ttr, 99)),
+            "p50_wait_for_admission_s": float(np.percentile(wait, 50)),
+            "p99_wait_for_admission_s": float(np.percentile(wait, 99)),
+            "busy_rejections": busy_rejects, "requests_per_s": len(reqs) / wall}
+
+
+def run_serve(args) -> int:
+    import torch
+
+    from paper_2012_05587_gb300 import workloads as W
+
+    prec = args.precision
+    reqs = W.serving_requests(args.requests, rate=args.rate, precision=prec)
+    free = torch.cuda.mem_get_info()[0]
+    budget = int(0.6 * free)
+    # a private stream: host reads of finished requests never wait for the batch
+    serve_stream = torch.cuda.Stream()
+    torch.cuda.set_stream(serve_stream)
+    sampler = B.ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    sat = _serve(reqs, prec, budget)
+    clocks = sampler.stop()
+    # the same request distribution at a fraction of the capacity just
+    # measured (requests completed per second while saturated), so that the
+    # times to result measure latency rather than queueing
+    low = None
+    if args.serve_low_frac > 0 and args.serve_low_requests > 0:
+        rate = args.serve_low_frac * sat["requests_per_s"]
+        reqs_low = W.serving_requests(args.serve_low_requests, rate=rate, run=1, precision=prec)
+        low = _serve(reqs_low, prec, budget)
+        low["arrival_rate_per_s"] = rate
+        low["what"] = (f"{len(reqs_low)} requests of the same distribution (another seed) arriving at "
+                       f"{args.serve_low_frac} of the capacity measured by the saturated run")
+    n_fp64 = args.fp64_sample if args.fp64_sample > 0 else 64
+    sample = stratified(reqs, n_fp64, lambda p: W.predicted_particles(p) * p["steps"])
+    fp64 = _fp64_one_at_a_time(sample, lambda p: p["steps"])
     line = {
-        "metric": B.METRIC, "value": ps / wall, "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 0,
+        "metric": B.METRIC, "value": sat["value"], "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 0,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec.startswith("fp32") else "f64", "data": "synthetic",
         "config": {"workload": f"serving: {len(reqs)} requests, Poisson arrivals {args.rate}/s, parameters from "
                                "the batch scan, steps U[500,5000], admission by predicted device footprint "
                                f"(budget {budget / 1e9:.1f} GB), continuous batching",
-                   "busy_rejections": busy_rejects, "wall_s": wall},
-        "p50_time_to_result_s": float(np.percentile(ttr, 50)),
-        "p99_time_to_result_s": float(np.percentile(ttr, 99)),
+                   "busy_rejections": sat["busy_rejections"], "wall_s": sat["wall_s"]},
+        "p50_time_to_result_s": sat["p50_time_to_result_s"],
+        "p99_time_to_result_s": sat["p99_time_to_result_s"],
+        "saturated": sat,
+        "below_capacity": low,
         "fp64_alone": dict(fp64, p50_s=float(np.percentile(fp64["per_request_s"], 50)),
                            p99_s=float(np.percentile(fp64["per_request_s"], 99)), per_request_s=None,
-                           sample=f"first {args.fp64_sample} requests, each alone in FP64"),
-        "served_over_fp64_alone": (ps / wall) / fp64["value"] if fp64["value"] else None,
+                           sample=_sample_note(len(sample), len(reqs), "requests")),
+        "served_over_fp64_alone": sat["value"] / fp64["value"] if fp64["value"] else None,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -199,6 +296,7 @@ def run_sweep(args) -> int:
         over = predicted > 2 * p0["particle_cap"]
         seeds = [0] if over else list(range(args.sweep_seeds))
         res = {"fp64": [], "fp32": [], "fp32_fine": []}
+        counts = {k: [] for k in res}
         errs = {}
         for run in seeds:
             p = W.precision_sweep(run=run)[idx]
@@ -210,7 +308,8 @@ def run_sweep(args) -> int:
                     with Cascade(q) as c:
                         c.step(p["steps"])
                         rec = c.diag(p["steps"])
-                    res[prec].append(analysis.ensemble(rec))
+                    res[prec].append(analysis.ensemble(rec, q))
+                    counts[prec].append({k: rec[k] for k in ("t", "n_elec", "n_posi")})
                 except CascadeError as e:
                     errs[prec] = str(e).split(":")[1].strip() if ":" in str(e) else str(e)
         row = {"E0": p0["E0"], "gamma_thr": p0["gamma_thr"], "dt": p0["dt"], "seeds": len(seeds),
@@ -219,6 +318,12 @@ def run_sweep(args) -> int:
             row["errors"] = errs
         else:
             mean = {k: {f: float(np.nanmean([r[f] for r in v])) for f in v[0]} for k, v in res.items()}
+            # the growth rate of the seed average of ln N, between counts fixed
+            # by the parameters (the same window for every precision)
+            win = analysis.growth_window(p0)
+            for k in mean:
+                mean[k]["growth_rate"] = analysis.seed_averaged_growth_rate(counts[k], win)
+            row["growth_window"] = list(win) if win else None
             row["fp64_mean"] = mean["fp64"]
             row["fp32_rel_err"] = analysis.relative_errors(mean["fp32"], mean["fp64"])
             row["fp32_fine_rel_err"] = analysis.relative_errors(mean["fp32_fine"], mean["fp64"])
@@ -226,6 +331,46 @@ def run_sweep(args) -> int:
         rows.append(row)
         print(json.dumps({"sweep_row": row}), flush=True)
     line = {"metric": B.METRIC, "value": None, "unit": UNIT, "workload": "precision sweep", "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_damping(args) -> int:
+    """Damping of the large-amplitude oscillation (Sections 5-6, Eq. 24):
+    the f = 0.1 cascade of workloads.damping_cascade over --damping-seeds
+    seeds in FP32-mixed, FP32-mixed-fine and FP64.  Reports per ensemble
+    diagnostic the FP64 mean and the relative error of each FP32 form with
+    its standard error from the seed-by-seed differences."""
+    import torch
+
+    from paper_2012_05587_gb300 import Cascade, analysis as A, workloads as W
+
+    t0 = time.perf_counter()
+    res = {"fp32": [], "fp32_fine": [], "fp64": []}
+    ps = {k: 0.0 for k in res}
+    secs = {k: 0.0 for k in res}
+    for run in range(args.damping_seeds):
+        for prec in res:
+            p = W.damping_cascade(run=run, precision=prec)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            with Cascade(p) as c:
+                c.step(p["steps"])
+                rec = c.diag(p["steps"])
+            torch.cuda.synchronize()
+            secs[prec] += time.perf_counter() - t1
+            ps[prec] += _psteps(rec)
+            res[prec].append(A.ensemble(rec, p))
+    keys = ("growth_rate", "screening_time", "peak_field_after_screening", "oscillation_frequency", "damping_rate",
+            "damping_eps0", "final_pairs", "final_energy")
+    p0 = W.damping_cascade()
+    line = {"metric": B.METRIC, "value": ps["fp32"] / secs["fp32"], "unit": UNIT,
+            "workload": f"damping cascade (f = 0.1, Nx = {p0['nx']}, {p0['steps']} steps), "
+                        f"{args.damping_seeds} seeds per precision",
+            "fp64_value": ps["fp64"] / secs["fp64"],
+            "fp32_vs_fp64": A.paired_comparison(res["fp32"], res["fp64"], keys),
+            "fp32_fine_vs_fp64": A.paired_comparison(res["fp32_fine"], res["fp64"], keys),
+            "seconds": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -372,4 +517,4 @@ def run_corotating(args) -> int:
 
 def run(args) -> int:
     return {"batch": run_batch, "serve": run_serve, "sweep": run_sweep, "paper": run_paper,
-            "corotating": run_corotating}[args.workload](args)
+            "corotating": run_corotating, "damping": run_damping}[args.workload](args)

@@ -144,6 +144,15 @@ int cascade_create_from_state(const cascade_params* params,
                               int64_t n_posi, const int32_t* cell_p, const double* off_p, const double* u_p,
                               const double* E_host, void* cuda_stream, cascade_t** out);
 
+/* As cascade_create_from_state, with FP32 host offsets and momenta: 12 B per
+ * particle to upload instead of 20, for FP32 cascades (whose particles are
+ * FP32 anyway; a two-word momentum gets a zero low word).  In CASCADE_FP64
+ * the values are widened exactly. */
+int cascade_create_from_state_f32(const cascade_params* params,
+                                  int64_t n_elec, const int32_t* cell_e, const float* off_e, const float* u_e,
+                                  int64_t n_posi, const int32_t* cell_p, const float* off_p, const float* u_p,
+                                  const double* E_host, void* cuda_stream, cascade_t** out);
+
 /* Advance nsteps steps (asynchronous).  One step n -> n+1 (Sections 2-3):
  *   1. photons due this step become e-/e+ pairs of gamma = eps_gamma/2 each,
  *      moving along the photon, at the conversion point x_emit +- l_pp;
@@ -173,6 +182,17 @@ int cascade_diag(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t* n
  * dx rho_i| of the current state (rho from the CIC shape); it is also stored
  * in the newest per-step record. */
 int cascade_gauss(cascade_t* h, double* resid_out);
+
+/* Per-step Gauss residual: with every > 0, each step whose index (after the
+ * step) is a multiple of every also deposits the CIC charge of all leptons
+ * and stores max_i |E_{i+1/2} - E_{i-1/2} - dx (rho_i - rho_GJ)| in that
+ * step's record (gauss_resid; NaN in the other records).  A charge-conserving
+ * step keeps the residual at round-off from one step to the next (Eq. 25,
+ * Section 3 with rho_GJ = 0), so a growing value shows a broken invariant.
+ * Cost: one more pass over the particles' cells and offsets (8 B in FP32)
+ * with FP64 atomics, and two launches per step.  0 (the default) turns it
+ * off.  The first call with every > 0 allocates nx + 1 doubles. */
+int cascade_set_gauss_every(cascade_t* h, int32_t every);
 
 /* Synchronise and copy particle counts, photons in flight and the step index. */
 int cascade_counts(cascade_t* h, int64_t* n_elec, int64_t* n_posi, int64_t* n_photon, int64_t* step);
@@ -261,6 +281,77 @@ int cascade_batch_release(cascade_batch_t* b, int32_t slot);
 
 /* Number of slots, occupied slots and device bytes held by members. */
 int cascade_batch_info(cascade_batch_t* b, int32_t* slots, int32_t* occupied, size_t* bytes_in_use);
+
+/* Launch variant of the batched particle kernel.  All variants compute the
+ * same step; they differ in speed, and in round-off through the fixed-point
+ * scale of each CTA's share of the batch. */
+typedef struct {
+  int32_t shape;        /* threads per CTA and register budget: 0 = 2 x 512 threads (64
+                           registers), 1 = 512 (128), 2 = 768 (80), 3 = 640 (96) */
+  int32_t stage;        /* 1: particles staged through shared memory with cp.async (FP32) */
+  int32_t prefetch;     /* iterations ahead each warp prefetches its particles into L2 (0..8) */
+  int32_t member_cost;  /* fixed work units per member in the partition (4-particle chunks) */
+} cascade_batch_variant;
+
+enum { CASCADE_VARIANT_DEFAULT = 0, CASCADE_VARIANT_CACHED = 1, CASCADE_VARIANT_TUNED = 2,
+       CASCADE_VARIANT_FORCED = 3 };
+
+/* Autotuning (the batches' launch shapes are picked by measurement).  A
+ * batch tunes at every cascade_batch_step or cascade_batch_run that has work
+ * and finds its size class (cascade_tune_key: grid, seed particles and
+ * member count of the members present) changed since the variant in use was
+ * picked -- at the first such call, and again as a server's occupancy moves
+ * to another class.  It first looks the class up in the per-device cache
+ * file (cascade_tune_cache_path); on a miss, after a warm-up
+ * (cascade_batch_tune_warmup), it runs the
+ * candidate variants -- the four shapes with cp.async staging (FP32) and
+ * without it (then an L2 prefetch) -- one batch step each, round after round
+ * (4 rounds, or as many as the call's steps allow), times the particle
+ * kernel with CUDA events, scores each variant by time per work unit of the
+ * partition, keeps the fastest and stores it in the cache.  Tuning steps are
+ * real steps of the members' work.  Setting any of CASCADE_BATCH_SHAPE,
+ * CASCADE_BATCH_STAGE, CASCADE_BATCH_PREFETCH, CASCADE_BATCH_MEMBER_COST
+ * before creation forces a variant (no tuning); CASCADE_BATCH_TUNE=0 keeps
+ * the default variant.
+ *   cascade_batch_set_variant  forces v (CASCADE_ERR_INVALID_ARG if it does not
+ *                              fit this batch) and disarms tuning
+ *   cascade_batch_get_variant  the variant in use, where it came from
+ *                              (CASCADE_VARIANT_*) and, when tuned, its
+ *                              measured ns per work unit (each nullable)
+ *   cascade_batch_tune_next    (re)arms tuning for the next step or run
+ *                              call: rounds of candidates (0 disarms);
+ *                              use_cache = 0 makes that pass measure even
+ *                              on a cache hit */
+int cascade_batch_set_variant(cascade_batch_t* b, const cascade_batch_variant* v);
+int cascade_batch_get_variant(cascade_batch_t* b, cascade_batch_variant* v, int32_t* source, double* ns_per_unit);
+int cascade_batch_tune_next(cascade_batch_t* b, int32_t rounds, int32_t use_cache);
+/* Steps a batch runs with its current variant before a tuning pass the
+ * cache cannot answer (default 256; cascade_batch_step uses at most a
+ * quarter of the steps it runs): the members then hold their grown particle
+ * counts rather than their seeds. */
+int cascade_batch_tune_warmup(cascade_batch_t* b, int64_t steps);
+/* The candidates of the batch's last tuning pass and their measured ns per
+ * work unit (up to max; *n_out = 0 before any pass). */
+int cascade_batch_tuning_report(cascade_batch_t* b, cascade_batch_variant* cands, double* ns_per_unit, int32_t max,
+                                int32_t* n_out);
+
+/* The tuning cache.  Key of a size class: precision, ceil(log2) of the
+ * largest member grid, the nearest log2 of the members' seed particles and
+ * ceil(log2) of the number of members (key_len >= 64).  The file holds one
+ * line per key: "<key>\t<shape> <stage> <prefetch> <member_cost>\t<ns per
+ * unit>"; a store rewrites it whole through a temporary file and a rename.
+ * Entries are also kept in memory for the process, so a path that cannot be
+ * written (or NULL) still serves lookups of this process's own stores.
+ * cascade_tune_cache_lookup sets *found to 1 and fills out on a hit.
+ * cascade_tune_cache_path: $CASCADE_TUNE_CACHE if set (empty = memory only),
+ * else $XDG_CACHE_HOME or $HOME/.cache, then
+ * cascade-gb300/batch-tune-<device name>-sm<cc>.txt for the current device
+ * (thread-local static storage). */
+int cascade_tune_key(int32_t precision, int32_t max_nx, int64_t particles, int32_t members, char* key_out,
+                     int32_t key_len);
+int cascade_tune_cache_lookup(const char* path, const char* key, cascade_batch_variant* out, int32_t* found);
+int cascade_tune_cache_store(const char* path, const char* key, const cascade_batch_variant* v, double ns_per_unit);
+const char* cascade_tune_cache_path(void);
 
 /* Kernel timing of a batch, as cascade_set_timing / cascade_timing: with
  * timing on, batch steps are launched directly (no graph replay) with a CUDA

@@ -159,6 +159,30 @@ def ensemble(rec: dict, params: dict | None = None) -> dict:
     return out
 
 
+def paired_comparison(runs: list, refs: list, keys=None) -> dict:
+    """Seed-by-seed comparison of two ensembles run from the same seeds
+    (ensemble dicts in the same seed order): per diagnostic the two means,
+    the relative difference of the means, and the standard error of that
+    relative difference from the spread of the per-seed differences (a
+    chaotic run departs from its twin after the parity horizon, so the means
+    differ by sampling noise as well as by any bias)."""
+    keys = keys or [k for k in refs[0] if k != "seed"]
+    out = {}
+    for k in keys:
+        a = np.array([r[k] for r in runs], float)
+        b = np.array([r[k] for r in refs], float)
+        m = np.isfinite(a) & np.isfinite(b)
+        if m.sum() < 2 or not np.isfinite(b[m].mean()) or b[m].mean() == 0:
+            out[k] = {"mean": float(np.nanmean(a)), "ref_mean": float(np.nanmean(b)), "rel_err": float("nan"),
+                      "rel_se": float("nan"), "n": int(m.sum())}
+            continue
+        d = a[m] - b[m]
+        ref = b[m].mean()
+        out[k] = {"mean": float(a[m].mean()), "ref_mean": float(ref), "rel_err": float(d.mean() / abs(ref)),
+                  "rel_se": float(d.std(ddof=1) / np.sqrt(m.sum()) / abs(ref)), "n": int(m.sum())}
+    return out
+
+
 def relative_errors(a: dict, ref: dict) -> dict:
     out = {}
     for k, v in ref.items():

@@ -26,6 +26,7 @@ UNITS = {
     "kernels_fp64.cu": ["-fmad=false"],
     "kernels_fp32.cu": [],
     "cascade_noalloc.cu": [],
+    "cascade_tune.cu": [],
 }
 
 

@@ -60,6 +60,13 @@ class cascade_diag_t(ctypes.Structure):
 DIAG_FIELDS = [f for f, _ in cascade_diag_t._fields_]
 DIAG_DTYPE = np.dtype([(f, np.int64 if t is ctypes.c_int64 else np.float64) for f, t in cascade_diag_t._fields_])
 
+class cascade_batch_variant(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("stage", ctypes.c_int32), ("prefetch", ctypes.c_int32),
+                ("member_cost", ctypes.c_int32)]
+
+
+VARIANT_SOURCES = {0: "default", 1: "cached", 2: "tuned", 3: "forced"}
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -93,10 +100,13 @@ def load() -> ctypes.CDLL:
             "cascade_create": ([P(cascade_params), vp, P(vp)], ctypes.c_int),
             "cascade_create_from_state": ([P(cascade_params), i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, P(vp)],
                                           ctypes.c_int),
+            "cascade_create_from_state_f32": ([P(cascade_params), i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, P(vp)],
+                                              ctypes.c_int),
             "cascade_step": ([vp, i32], ctypes.c_int),
             "cascade_sync": ([vp], ctypes.c_int),
             "cascade_diag": ([vp, vp, i32, P(i32), vp, vp], ctypes.c_int),
             "cascade_gauss": ([vp, P(f64)], ctypes.c_int),
+            "cascade_set_gauss_every": ([vp, i32], ctypes.c_int),
             "cascade_counts": ([vp, P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
             "cascade_particles": ([vp, i32, i64, vp, vp, vp, P(i64)], ctypes.c_int),
             "cascade_histogram": ([vp, i32, i32, i32, f64, f64, vp], ctypes.c_int),
@@ -119,6 +129,17 @@ def load() -> ctypes.CDLL:
             "cascade_batch_info": ([vp, P(i32), P(i32), P(ctypes.c_size_t)], ctypes.c_int),
             "cascade_batch_destroy": ([vp], ctypes.c_int),
             "cascade_batch_set_timing": ([vp, i32], ctypes.c_int),
+            "cascade_batch_set_variant": ([vp, P(cascade_batch_variant)], ctypes.c_int),
+            "cascade_batch_get_variant": ([vp, P(cascade_batch_variant), P(i32), P(f64)], ctypes.c_int),
+            "cascade_batch_tune_next": ([vp, i32, i32], ctypes.c_int),
+            "cascade_batch_tune_warmup": ([vp, i64], ctypes.c_int),
+            "cascade_batch_tuning_report": ([vp, P(cascade_batch_variant), P(f64), i32, P(i32)], ctypes.c_int),
+            "cascade_tune_key": ([i32, i32, i64, i32, ctypes.c_char_p, i32], ctypes.c_int),
+            "cascade_tune_cache_lookup": ([ctypes.c_char_p, ctypes.c_char_p, P(cascade_batch_variant), P(i32)],
+                                          ctypes.c_int),
+            "cascade_tune_cache_store": ([ctypes.c_char_p, ctypes.c_char_p, P(cascade_batch_variant), f64],
+                                         ctypes.c_int),
+            "cascade_tune_cache_path": ([], ctypes.c_char_p),
             "cascade_batch_timing": ([vp, P(f64), P(i64), P(i64)], ctypes.c_int),
             "cascade_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "cascade_last_error_message": ([], ctypes.c_char_p),
@@ -205,15 +226,22 @@ def cascade_create(params: dict, stream: int = 0) -> ctypes.c_void_p:
 
 
 def cascade_create_from_state(params: dict, elec: dict, posi: dict, E=None, stream: int = 0) -> ctypes.c_void_p:
+    """Explicit state from host arrays: FP32 offsets and momenta in both
+    species go through cascade_create_from_state_f32, anything else through
+    cascade_create_from_state (FP64)."""
+    f32 = all(np.asarray(s[k]).dtype == np.float32 for s in (elec, posi) for k in ("off", "u"))
+    real = np.float32 if f32 else np.float64
+
     def arrays(s):
-        return (np.ascontiguousarray(s["cell"], np.int32), np.ascontiguousarray(s["off"], np.float64),
-                np.ascontiguousarray(s["u"], np.float64))
+        return (np.ascontiguousarray(s["cell"], np.int32), np.ascontiguousarray(s["off"], real),
+                np.ascontiguousarray(s["u"], real))
     ce, oe, ue = arrays(elec)
     cp_, op, up = arrays(posi)
     E = None if E is None else np.ascontiguousarray(E, np.float64)
     h = ctypes.c_void_p()
     cp = make_params(params)
-    check("cascade_create_from_state", load().cascade_create_from_state(
+    name = "cascade_create_from_state_f32" if f32 else "cascade_create_from_state"
+    check(name, getattr(load(), name)(
         ctypes.byref(cp), len(ce), _ptr(ce), _ptr(oe), _ptr(ue), len(cp_), _ptr(cp_), _ptr(op), _ptr(up),
         _ptr(E), ctypes.c_void_p(stream), ctypes.byref(h)))
     return h
@@ -246,6 +274,10 @@ def cascade_gauss(h) -> float:
     r = ctypes.c_double()
     check("cascade_gauss", load().cascade_gauss(h, ctypes.byref(r)))
     return r.value
+
+
+def cascade_set_gauss_every(h, every: int) -> None:
+    check("cascade_set_gauss_every", load().cascade_set_gauss_every(h, int(every)))
 
 
 def cascade_counts(h) -> dict:
@@ -410,6 +442,66 @@ def cascade_batch_timing(b) -> dict:
     k = ctypes.c_int64()
     check("cascade_batch_timing", load().cascade_batch_timing(b, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)))
     return {"particle_kernel_ms": ms.value, "particle_kernel_launches": n.value, "kernels_launched": k.value}
+
+
+def _variant_dict(v) -> dict:
+    return {"shape": v.shape, "stage": v.stage, "prefetch": v.prefetch, "member_cost": v.member_cost}
+
+
+def cascade_batch_set_variant(b, shape: int, stage: int, prefetch: int, member_cost: int = 1024) -> None:
+    v = cascade_batch_variant(shape, stage, prefetch, member_cost)
+    check("cascade_batch_set_variant", load().cascade_batch_set_variant(b, ctypes.byref(v)))
+
+
+def cascade_batch_get_variant(b) -> dict:
+    v = cascade_batch_variant()
+    src = ctypes.c_int32()
+    ns = ctypes.c_double()
+    check("cascade_batch_get_variant", load().cascade_batch_get_variant(b, ctypes.byref(v), ctypes.byref(src),
+                                                                        ctypes.byref(ns)))
+    return dict(_variant_dict(v), source=VARIANT_SOURCES.get(src.value, src.value), ns_per_unit=ns.value)
+
+
+def cascade_batch_tune_next(b, rounds: int = 4, use_cache: bool = True) -> None:
+    check("cascade_batch_tune_next", load().cascade_batch_tune_next(b, int(rounds), 1 if use_cache else 0))
+
+
+def cascade_batch_tune_warmup(b, steps: int) -> None:
+    check("cascade_batch_tune_warmup", load().cascade_batch_tune_warmup(b, int(steps)))
+
+
+def cascade_batch_tuning_report(b) -> list:
+    cands = (cascade_batch_variant * 16)()
+    ns = (ctypes.c_double * 16)()
+    n = ctypes.c_int32()
+    check("cascade_batch_tuning_report", load().cascade_batch_tuning_report(b, cands, ns, 16, ctypes.byref(n)))
+    return [dict(_variant_dict(cands[i]), ns_per_unit=ns[i]) for i in range(n.value)]
+
+
+def cascade_tune_key(precision, max_nx: int, particles: int, members: int) -> str:
+    buf = ctypes.create_string_buffer(128)
+    check("cascade_tune_key", load().cascade_tune_key(_prec_code(precision), int(max_nx), int(particles),
+                                                      int(members), buf, len(buf)))
+    return buf.value.decode()
+
+
+def cascade_tune_cache_lookup(path, key: str):
+    v = cascade_batch_variant()
+    found = ctypes.c_int32()
+    check("cascade_tune_cache_lookup", load().cascade_tune_cache_lookup(
+        None if path is None else str(path).encode(), key.encode(), ctypes.byref(v), ctypes.byref(found)))
+    return _variant_dict(v) if found.value else None
+
+
+def cascade_tune_cache_store(path, key: str, shape: int, stage: int, prefetch: int, member_cost: int,
+                             ns_per_unit: float) -> None:
+    v = cascade_batch_variant(shape, stage, prefetch, member_cost)
+    check("cascade_tune_cache_store", load().cascade_tune_cache_store(
+        None if path is None else str(path).encode(), key.encode(), ctypes.byref(v), float(ns_per_unit)))
+
+
+def cascade_tune_cache_path() -> str:
+    return load().cascade_tune_cache_path().decode()
 
 
 def cascade_batch_destroy(b) -> None:

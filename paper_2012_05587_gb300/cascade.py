@@ -50,6 +50,9 @@ class Cascade:
     def gauss(self) -> float:
         return capi.cascade_gauss(self.h)
 
+    def set_gauss_every(self, every: int) -> None:
+        capi.cascade_set_gauss_every(self.h, every)
+
     def counts(self) -> dict:
         return capi.cascade_counts(self.h)
 
@@ -134,6 +137,20 @@ class CascadeBatch:
 
     def info(self) -> dict:
         return capi.cascade_batch_info(self.b)
+
+    def variant(self) -> dict:
+        return capi.cascade_batch_get_variant(self.b)
+
+    def set_variant(self, shape: int, stage: int, prefetch: int, member_cost: int = 1024) -> None:
+        capi.cascade_batch_set_variant(self.b, shape, stage, prefetch, member_cost)
+
+    def tune_next(self, rounds: int = 4, use_cache: bool = True, warmup: int | None = None) -> None:
+        if warmup is not None:
+            capi.cascade_batch_tune_warmup(self.b, warmup)
+        capi.cascade_batch_tune_next(self.b, rounds, use_cache)
+
+    def tuning_report(self) -> list:
+        return capi.cascade_batch_tuning_report(self.b)
 
     def close(self) -> None:
         if getattr(self, "b", None):

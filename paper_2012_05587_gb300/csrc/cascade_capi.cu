@@ -8,6 +8,7 @@
 
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "cascade_internal.h"
@@ -155,7 +156,7 @@ struct cascade {
       }
       cudaEvent_t b = ev_pool[ev_used], a = ev_pool[ev_used + 1];
       ev_used += 2;
-      kernels_launched += 3;
+      kernels_launched += 3 + (d.gauss_every > 0 ? 2 : 0) + (d.open_bc ? 2 : 0);
       return p.precision == CASCADE_FP64 ? step_timed_fp64(d, stream, b, a) : step_timed_fp32(d, stream, b, a);
     }
     return p.precision == CASCADE_FP64 ? step_fp64(d, stream) : step_fp32(d, stream);
@@ -311,13 +312,14 @@ int upload_E(cascade_t* h, const double* E_host) {
   return CASCADE_OK;
 }
 
-// Copy one species from host arrays: cells straight into place, offsets and
-// momenta through a device staging buffer in chunks; a kernel rounds them to
-// the particle precision and checks every particle.
-int upload_species(cascade_t* h, int s, long long n, const int32_t* cell, const double* off, const double* u) {
+// Copy one species from host arrays (H = double or float): cells straight
+// into place, offsets and momenta through a device staging buffer in chunks;
+// a kernel rounds them to the particle precision and checks every particle.
+template <class H>
+int upload_species(cascade_t* h, int s, long long n, const int32_t* cell, const H* off, const H* u) {
   if (n == 0) return CASCADE_OK;
   const long long chunk = n < (1LL << 23) ? n : (1LL << 23);
-  const size_t stage_bytes = sizeof(double) * (size_t)chunk;
+  const size_t stage_bytes = sizeof(H) * (size_t)chunk;
   void* stage = nullptr;
   if (h->alloc_fn) {
     stage = h->alloc_fn(2 * stage_bytes, (void*)h->stream, h->alloc_ctx);
@@ -326,8 +328,9 @@ int upload_species(cascade_t* h, int s, long long n, const int32_t* cell, const 
     stage = nullptr;
   }
   if (!stage) return CASCADE_ERR_OOM;
-  double* so = static_cast<double*>(stage);
-  double* su = so + chunk;
+  H* so = static_cast<H*>(stage);
+  H* su = so + chunk;
+  const int f32 = sizeof(H) == sizeof(float) ? 1 : 0;
   unsigned int* bad = reinterpret_cast<unsigned int*>(h->scalar);
   unsigned int nbad = 0;
   cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), h->stream);
@@ -335,11 +338,11 @@ int upload_species(cascade_t* h, int s, long long n, const int32_t* cell, const 
     e = cudaMemcpyAsync(h->d.cell[s], cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream);
   for (long long k = 0; k < n && e == cudaSuccess; k += chunk) {
     const long long m = (n - k) < chunk ? (n - k) : chunk;
-    e = cudaMemcpyAsync(so, off + k, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(su, u + k, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream);
+    e = cudaMemcpyAsync(so, off + k, sizeof(H) * m, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(su, u + k, sizeof(H) * m, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-      e = h->real_size == sizeof(double) ? upload_fp64(h->d, s, k, m, so, su, bad, h->stream)
-                                         : upload_fp32(h->d, s, k, m, so, su, bad, h->stream);
+      e = h->real_size == sizeof(double) ? upload_fp64(h->d, s, k, m, so, su, f32, bad, h->stream)
+                                         : upload_fp32(h->d, s, k, m, so, su, f32, bad, h->stream);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -472,6 +475,32 @@ int cascade_create_from_state(const cascade_params* params, int64_t n_elec, cons
   return CASCADE_OK;
 }
 
+int cascade_create_from_state_f32(const cascade_params* params, int64_t n_elec, const int32_t* cell_e,
+                                  const float* off_e, const float* u_e, int64_t n_posi, const int32_t* cell_p,
+                                  const float* off_p, const float* u_p, const double* E_host, void* cuda_stream,
+                                  cascade_t** out) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!out || n_elec < 0 || n_posi < 0) return CASCADE_ERR_INVALID_ARG;
+  if ((n_elec > 0 && (!cell_e || !off_e || !u_e)) || (n_posi > 0 && (!cell_p || !off_p || !u_p)))
+    return CASCADE_ERR_INVALID_ARG;
+  cascade_t* h = nullptr;
+  int rc = setup(params, cuda_stream, &h);
+  if (rc == CASCADE_OK && (n_elec > params->particle_cap || n_posi > params->particle_cap)) {
+    snprintf(g_msg, sizeof(g_msg), "state exceeds particle_cap");
+    rc = CASCADE_ERR_CAPACITY;
+  }
+  if (rc == CASCADE_OK) rc = upload_E(h, E_host);
+  if (rc == CASCADE_OK) rc = upload_species(h, 0, n_elec, cell_e, off_e, u_e);
+  if (rc == CASCADE_OK) rc = upload_species(h, 1, n_posi, cell_p, off_p, u_p);
+  if (rc == CASCADE_OK) rc = set_counts(h, n_elec, n_posi);
+  if (rc != CASCADE_OK) {
+    cascade_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return CASCADE_OK;
+}
+
 int cascade_step(cascade_t* h, int32_t nsteps) {
   g_msg[0] = '\0';  // a message describes this call only
   if (!h || nsteps < 0) return CASCADE_ERR_INVALID_ARG;
@@ -531,6 +560,25 @@ int cascade_diag(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t* n
   if (E_host && (rc = d2h(h, E_host, h->d.E, sizeof(double) * h->d.nx))) return rc;
   if (J_host && (rc = d2h(h, J_host, h->d.J, sizeof(double) * h->d.nx))) return rc;
   return h->sticky;
+}
+
+int cascade_set_gauss_every(cascade_t* h, int32_t every) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!h || every < 0) return CASCADE_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  if (every > 0 && !h->d.gauss_rho) {
+    h->d.gauss_rho = static_cast<double*>(h->dalloc(sizeof(double) * h->d.nx));
+    h->d.gauss_out = static_cast<double*>(h->dalloc(sizeof(double)));
+    if (!h->d.gauss_rho || !h->d.gauss_out) return CASCADE_ERR_OOM;
+    CUDA_TRY(cudaMemsetAsync(h->d.gauss_rho, 0, sizeof(double) * h->d.nx, h->stream));
+  }
+  if (every != h->d.gauss_every && h->graph) {  // the captured step no longer matches
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  h->d.gauss_every = every;
+  return CASCADE_OK;
 }
 
 int cascade_gauss(cascade_t* h, double* resid_out) {
@@ -752,6 +800,10 @@ struct cascade_batch {
   long long* h_snap[kSnapRing] = {nullptr};
   cudaEvent_t ev_snap[kSnapRing] = {nullptr};
   long long snap_seq[kSnapRing] = {0};
+  // the newest snapshot seen landed (copied out of the ring before its slot
+  // is reused, so a host that runs ahead of the GPU still sees completions)
+  std::vector<long long> landed;
+  long long landed_seq = 0;
   long long run_seq = 0;               // runs enqueued so far
   int snap_next = 0;
   cudaEvent_t ev_init = nullptr;
@@ -763,6 +815,20 @@ struct cascade_batch {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   long long kernels_launched = 0;
+  // launch variant of the particle kernel and its autotuning
+  cascade_batch_variant var{};
+  int var_source = CASCADE_VARIANT_DEFAULT;
+  double var_ns_per_unit = 0.0;
+  bool tune_auto = false;              // tune when the size class changes (at a step or run with work)
+  long long tune_warmup = 256;         // steps run before a pass that the cache cannot answer
+  int tune_rounds = 4;                 // rounds of candidates per tuning pass
+  int tune_use_cache = 1;              // 0: the next pass measures even on a cache hit
+  std::string tuned_key;               // size class of the variant in use ("" = none yet)
+  long long tune_countdown = -1;       // steps left before a pending tuning pass (-1: none pending)
+  std::vector<cascade_batch_variant> tune_cands;  // the last pass's candidates ...
+  std::vector<double> tune_ns;                    // ... and their ns per work unit
+  long long* d_units = nullptr;        // work units of each tuning step (device)
+  long long seed_particles = 0;        // seed particles of the members (size class of the batch)
 
   cudaError_t launch_step() {
     cudaEvent_t before = nullptr, after = nullptr;
@@ -785,6 +851,164 @@ struct cascade_batch {
 
 namespace {
 
+constexpr int kTuneMaxSteps = 256;  // tuning steps logged per tuning pass
+
+// Launch parameters of one variant (no graph change); CASCADE_ERR_INVALID_ARG
+// when the variant does not fit this batch (staging beside a large grid, a
+// form the precision has no kernel for).
+int batch_config_variant(cascade_batch_t* b, const cascade_batch_variant& v) {
+  if (v.shape < 0 || v.shape > 3 || (v.stage != 0 && v.stage != 1) || v.prefetch < 0 || v.prefetch > 8 ||
+      v.member_cost < 0)
+    return CASCADE_ERR_INVALID_ARG;
+  const int fine = b->precision == CASCADE_FP32_MIXED_FINE ? 1 : 0;
+  int grid = 0, block = 0, dep = 0;
+  size_t smem = 0;
+  const cudaError_t e =
+      b->precision == CASCADE_FP64
+          ? batch_configure_fp64(b->max_nx, 0, b->num_sms, v.shape, v.stage, &grid, &block, &smem, &dep)
+          : batch_configure_fp32(b->max_nx, fine, b->num_sms, v.shape, v.stage, &grid, &block, &smem, &dep);
+  if (e == cudaErrorInvalidValue) return CASCADE_ERR_INVALID_ARG;
+  if (e != cudaSuccess) return cuda_fail(e, "batch configure");
+  b->grid = grid;
+  b->block = block;
+  b->smem = smem;
+  b->dep = dep;
+  b->bd.prefetch = v.prefetch;
+  b->bd.member_cost = v.member_cost;
+  return CASCADE_OK;
+}
+
+// Make v the batch's variant; a captured graph of the old one is dropped.
+int batch_apply_variant(cascade_batch_t* b, const cascade_batch_variant& v, int source, double ns_per_unit) {
+  const int rc = batch_config_variant(b, v);
+  if (rc) return rc;
+  b->var = v;
+  b->var_source = source;
+  b->var_ns_per_unit = ns_per_unit;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return CASCADE_OK;
+}
+
+int batch_occupied(const cascade_batch_t* b) {
+  int occ = 0;
+  for (cascade_t* h : b->members) occ += h != nullptr;
+  return occ;
+}
+
+// Autotuning (spec pattern 2): the candidates -- the four launch shapes
+// with the particles staged through shared memory (FP32) and without it,
+// then with an L2 prefetch one iteration ahead -- run in turn, one batch step
+// each, round after round, so that each is measured over the same stretch of
+// the run (the particle counts grow during a cascade).  Every tuning step is
+// a real step of the members' work.  The score is the particle kernel's time
+// (CUDA events) per work unit of the partition (4-particle chunks plus the
+// fixed share per member, logged from the plan kernel every step); the
+// fastest candidate is kept and stored in the cache under the batch's size
+// class.  Runs at most max_steps steps; returns the number run in *used.
+int batch_tune(cascade_batch_t* b, long long max_steps, long long* used) {
+  *used = 0;
+  if (!b->tune_auto || batch_occupied(b) == 0) return CASCADE_OK;
+  char key[128];
+  int rc = cascade_tune_key(b->precision, b->max_nx, b->seed_particles, batch_occupied(b), key, sizeof(key));
+  if (rc) return rc;
+  if (b->tuned_key == key) return CASCADE_OK;  // the variant in use was picked for this size class
+  const char* path = cascade_tune_cache_path();
+  if (b->tune_use_cache) {
+    cascade_batch_variant v{};
+    int32_t found = 0;
+    cascade_tune_cache_lookup(path, key, &v, &found);
+    if (found && batch_apply_variant(b, v, CASCADE_VARIANT_CACHED, 0.0) == CASCADE_OK) {
+      b->tuned_key = key;
+      b->tune_countdown = -1;
+      return CASCADE_OK;
+    }
+  }
+  // a miss: measure once the members have grown past their seeds (a cascade
+  // multiplies its particles many times in its first steps, and the variant
+  // that wins on the seeds is not the one that wins on the grown state)
+  if (b->tune_countdown < 0) b->tune_countdown = b->tune_warmup;
+  if (b->tune_countdown > 0) return CASCADE_OK;
+  std::vector<cascade_batch_variant> cand;
+  for (int stage = 1; stage >= 0; --stage)
+    for (int shape : {3, 2, 1, 0}) {
+      const cascade_batch_variant v{shape, stage, stage ? 0 : 1, 1024};
+      if (batch_config_variant(b, v) == CASCADE_OK) cand.push_back(v);
+    }
+  if (cand.empty()) return CASCADE_ERR_INVALID_ARG;
+  const int V = (int)cand.size();
+  long long steps = (long long)V * b->tune_rounds;
+  if (steps > max_steps) steps = max_steps;
+  if (steps > kTuneMaxSteps) steps = kTuneMaxSteps;
+  if (steps < V) {  // too few steps to measure every candidate: keep the current variant
+    return CASCADE_OK;
+  }
+  // direct launches with an event pair around each particle kernel
+  const bool was_timing = b->timing;
+  const size_t ev0 = b->ev_used;
+  b->timing = true;
+  for (long long k = 0; k < steps; ++k) {
+    rc = batch_config_variant(b, cand[k % V]);
+    if (rc) break;
+    cudaError_t e = b->launch_step();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_units + k, b->d_item_start + b->n_slots, sizeof(long long), cudaMemcpyDeviceToDevice,
+                          b->stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "tuning step");
+      break;
+    }
+    *used = k + 1;
+  }
+  b->timing = was_timing;
+  std::vector<long long> units(kTuneMaxSteps, 0);
+  std::vector<double> ms(V, 0.0), un(V, 0.0);
+  if (rc == CASCADE_OK) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(units.data(), b->d_units, sizeof(long long) * (size_t)*used, cudaMemcpyDeviceToHost);
+    for (long long k = 0; k < *used && e == cudaSuccess; ++k) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, b->ev_pool[ev0 + 2 * k], b->ev_pool[ev0 + 2 * k + 1]);
+      ms[k % V] += t;
+      un[k % V] += (double)units[k];
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "tuning events");
+  }
+  // the tuning events are not part of the caller's timing
+  b->ev_used = ev0;
+  if (!was_timing) b->kernels_launched = 0;
+  if (rc) {
+    batch_config_variant(b, b->var);
+    return rc;
+  }
+  int best = -1;
+  double best_ns = 0.0;
+  for (int v = 0; v < V; ++v) {
+    if (!(un[v] > 0)) continue;
+    const double ns = 1e6 * ms[v] / un[v];
+    if (best < 0 || ns < best_ns) {
+      best = v;
+      best_ns = ns;
+    }
+  }
+  if (best < 0) {  // no work was measured (idle members): keep the current variant
+    batch_config_variant(b, b->var);
+    return CASCADE_OK;
+  }
+  cascade_tune_cache_store(path, key, &cand[best], best_ns);
+  g_msg[0] = '\0';  // an unwritable cache is not this call's failure
+  b->tuned_key = key;
+  b->tune_use_cache = 1;
+  b->tune_countdown = -1;
+  b->tune_cands = cand;
+  b->tune_ns.assign(V, 0.0);
+  for (int v = 0; v < V; ++v) b->tune_ns[v] = un[v] > 0 ? 1e6 * ms[v] / un[v] : 0.0;
+  return batch_apply_variant(b, cand[best], CASCADE_VARIANT_TUNED, best_ns);
+}
+
 int batch_capture(cascade_batch_t* b) {
   if (!b->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
@@ -805,6 +1029,13 @@ int batch_capture(cascade_batch_t* b) {
   return CASCADE_OK;
 }
 
+// A snapshot slot whose copy has landed: keep it if it is the newest seen.
+void batch_harvest(cascade_batch_t* b, int k) {
+  if (b->snap_seq[k] <= b->landed_seq) return;
+  b->landed.assign(b->h_snap[k], b->h_snap[k] + b->n_slots);
+  b->landed_seq = b->snap_seq[k];
+}
+
 // Queue nsteps batch steps and a snapshot of the remaining counts.
 int batch_enqueue(cascade_batch_t* b, int nsteps) {
   int left = nsteps;
@@ -823,6 +1054,7 @@ int batch_enqueue(cascade_batch_t* b, int nsteps) {
   const int k = b->snap_next;
   // the slot's previous snapshot must have landed before it is overwritten
   CUDA_TRY(cudaEventSynchronize(b->ev_snap[k]));
+  if (b->snap_seq[k]) batch_harvest(b, k);
   b->run_seq += 1;
   CUDA_TRY(cudaMemcpyAsync(b->h_snap[k], b->d_remaining, sizeof(long long) * b->n_slots, cudaMemcpyDeviceToHost,
                            b->stream));
@@ -838,6 +1070,30 @@ int batch_member_check(cascade_batch_t* b, int slot) {
 }
 
 bool same_kernel_class(int a, int c) { return (a == CASCADE_FP64) == (c == CASCADE_FP64) && a == c; }
+
+// Tuning inside a call that has *steps steps to run: a size class the cache
+// cannot answer is measured after warmup steps of the current variant (which
+// may span several calls); the steps run here are taken off *steps.
+int batch_tune_with_warmup(cascade_batch_t* b, long long* steps, long long warmup) {
+  long long used = 0;
+  int rc = batch_tune(b, *steps, &used);  // a cache hit, or arms the countdown
+  if (rc || b->tune_countdown < 0) {
+    *steps -= used;
+    return rc;
+  }
+  if (b->tune_countdown > warmup) b->tune_countdown = warmup;
+  if (b->tune_countdown > 0) {
+    const long long w = b->tune_countdown < *steps ? b->tune_countdown : *steps;
+    if ((rc = batch_enqueue(b, (int)w))) return rc;
+    *steps -= w;
+    b->tune_countdown -= w;
+  }
+  if (b->tune_countdown == 0 && *steps > 0) {
+    rc = batch_tune(b, *steps, &used);
+    *steps -= used;
+  }
+  return rc;
+}
 
 // Batch members keep one-word FP32 momenta (the batched particle kernel has
 // no two-word form).
@@ -884,27 +1140,65 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGetDevice"));
   e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
-  const int fine = precision == CASCADE_FP32_MIXED_FINE ? 1 : 0;
-  e = precision == CASCADE_FP64
-          ? batch_configure_fp64(max_nx, 0, b->num_sms, &b->grid, &b->block, &b->smem, &b->dep)
-          : batch_configure_fp32(max_nx, fine, b->num_sms, &b->grid, &b->block, &b->smem, &b->dep);
-  if (e == cudaErrorInvalidValue) {
-    snprintf(g_msg, sizeof(g_msg), "max_nx = %d does not fit the batch kernel's shared memory", max_nx);
-    return fail(CASCADE_ERR_INVALID_ARG);
+  // default variant: 640 threads at 96 registers, the particles staged
+  // through shared memory where that fits (FP32), else an L2 prefetch one
+  // iteration ahead (measured best on the 256-cascade scan)
+  {
+    const int st = precision == CASCADE_FP64 ? 0 : 1;
+    cascade_batch_variant v{3, st, st ? 0 : 1, 1024};
+    int rc = batch_config_variant(b, v);
+    if (rc == CASCADE_ERR_INVALID_ARG && v.stage) {
+      v.stage = 0;
+      v.prefetch = 1;
+      rc = batch_config_variant(b, v);
+    }
+    if (rc == CASCADE_ERR_INVALID_ARG) {
+      snprintf(g_msg, sizeof(g_msg), "max_nx = %d does not fit the batch kernel's shared memory", max_nx);
+      return fail(CASCADE_ERR_INVALID_ARG);
+    }
+    if (rc) return fail(rc);
+    b->var = v;
+    b->var_source = CASCADE_VARIANT_DEFAULT;
+    // forced picks for measurements: any of these variables fixes the
+    // variant and turns tuning off
+    const char* names[4] = {"CASCADE_BATCH_SHAPE", "CASCADE_BATCH_STAGE", "CASCADE_BATCH_PREFETCH",
+                            "CASCADE_BATCH_MEMBER_COST"};
+    int32_t* fields[4] = {&v.shape, &v.stage, &v.prefetch, &v.member_cost};
+    bool forced = false;
+    for (int i = 0; i < 4; ++i) {
+      const char* ev = getenv(names[i]);
+      if (ev && *ev) {
+        *fields[i] = atoi(ev);
+        forced = true;
+      }
+    }
+    if (forced) {
+      if (getenv("CASCADE_BATCH_STAGE") && !getenv("CASCADE_BATCH_PREFETCH")) v.prefetch = v.stage ? 0 : 1;
+      if ((rc = batch_config_variant(b, v))) {
+        snprintf(g_msg, sizeof(g_msg), "the forced batch variant (CASCADE_BATCH_*) does not fit this batch");
+        return fail(rc);
+      }
+      b->var = v;
+      b->var_source = CASCADE_VARIANT_FORCED;
+    } else {
+      const char* tune = getenv("CASCADE_BATCH_TUNE");
+      b->tune_auto = !(tune && *tune && atoi(tune) == 0);
+    }
   }
-  if (e != cudaSuccess) return fail(cuda_fail(e, "batch configure"));
   // device tables in one allocation
   const size_t n = (size_t)max_slots;
   const size_t b_devs = (sizeof(Dev) * n + 255) & ~size_t(255);
   const size_t b_rem = (sizeof(long long) * n + 255) & ~size_t(255);
   const size_t b_items = (sizeof(long long) * (n + 1) + 255) & ~size_t(255);
-  const size_t total = b_devs + b_rem + b_items;
+  const size_t b_units = sizeof(long long) * kTuneMaxSteps;
+  const size_t total = b_devs + b_rem + b_items + b_units;
   e = cudaMalloc(&b->d_block, total);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc batch tables"));
   char* base = static_cast<char*>(b->d_block);
   b->d_devs = reinterpret_cast<Dev*>(base);
   b->d_remaining = reinterpret_cast<long long*>(base + b_devs);
   b->d_item_start = reinterpret_cast<long long*>(base + b_devs + b_rem);
+  b->d_units = reinterpret_cast<long long*>(base + b_devs + b_rem + b_items);
   if ((e = cudaMemsetAsync(b->d_block, 0, total, b->stream)) != cudaSuccess) return fail(cuda_fail(e, "memset"));
   if ((e = cudaMallocHost(&b->h_devs, sizeof(Dev) * n)) != cudaSuccess) return fail(cuda_fail(e, "host mirror"));
   memset(b->h_devs, 0, sizeof(Dev) * n);
@@ -924,16 +1218,8 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
   b->bd.item_start = b->d_item_start;
   b->bd.n = max_slots;
   b->bd.max_nx = max_nx;
-  {
-    const char* env = getenv("CASCADE_BATCH_PREFETCH");  // measurement override
-    // measured on the 256-cascade scan: with the particles staged through
-    // shared memory (b->dep / 64 != 0) an L2 prefetch on top costs 9%;
-    // without staging, one iteration ahead is best
-    const int staged = (b->dep / 64) != 0;
-    b->bd.prefetch = (env && *env) ? atoi(env) : (staged ? 0 : 1);
-    const char* mc = getenv("CASCADE_BATCH_MEMBER_COST");  // measurement override
-    b->bd.member_cost = (mc && *mc) ? atoll(mc) : 1024;  // measured: 256 to 4096 perform alike
-  }
+  b->bd.prefetch = b->var.prefetch;
+  b->bd.member_cost = b->var.member_cost;
   if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return fail(cuda_fail(e, "sync"));
   *out = b;
   return CASCADE_OK;
@@ -980,6 +1266,7 @@ int cascade_batch_admit(cascade_batch_t* b, const cascade_params* params, int32_
   if (rc) return rc;
   b->members[slot] = h;
   b->used += h->bytes;
+  b->seed_particles += 2LL * params->nx * params->ppc;
   b->reported[slot] = 0;
   b->admit_seq[slot] = b->run_seq;
   // publish the member: its initialisation (on the private stream) happens
@@ -1064,6 +1351,10 @@ int cascade_batch_step(cascade_batch_t* b, const int32_t* nsteps_each) {
   }
   CUDA_TRY(cudaMemcpyAsync(b->d_remaining, b->h_set, sizeof(long long) * b->n_slots, cudaMemcpyHostToDevice,
                            b->stream));
+  if (b->tune_auto && most > 0) {
+    int rc = batch_tune_with_warmup(b, &most, (most / 4 < b->tune_warmup) ? most / 4 : b->tune_warmup);
+    if (rc) return rc;
+  }
   while (most > 0) {
     const int k = most > (1 << 30) ? (1 << 30) : (int)most;
     int rc = batch_enqueue(b, k);
@@ -1077,38 +1368,98 @@ int cascade_batch_run(cascade_batch_t* b, int32_t nsteps) {
   g_msg[0] = '\0';  // a message describes this call only
   if (!b || nsteps < 0) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(b->device);
+  if (b->tune_auto && nsteps > 0) {
+    long long left = nsteps;
+    const int rc = batch_tune_with_warmup(b, &left, b->tune_warmup);
+    if (rc) return rc;
+    nsteps = (int32_t)left;
+  }
   return batch_enqueue(b, nsteps);
+}
+
+int cascade_batch_set_variant(cascade_batch_t* b, const cascade_batch_variant* v) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!b || !v) return CASCADE_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  const int rc = batch_apply_variant(b, *v, CASCADE_VARIANT_FORCED, 0.0);
+  if (rc == CASCADE_ERR_INVALID_ARG) {
+    snprintf(g_msg, sizeof(g_msg), "variant (shape %d, stage %d, prefetch %d, member cost %d) does not fit this batch",
+             v->shape, v->stage, v->prefetch, v->member_cost);
+    batch_config_variant(b, b->var);
+    return rc;
+  }
+  if (rc == CASCADE_OK) b->tune_auto = false;
+  return rc;
+}
+
+int cascade_batch_get_variant(cascade_batch_t* b, cascade_batch_variant* v, int32_t* source, double* ns_per_unit) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!b) return CASCADE_ERR_INVALID_ARG;
+  if (v) *v = b->var;
+  if (source) *source = b->var_source;
+  if (ns_per_unit) *ns_per_unit = b->var_ns_per_unit;
+  return CASCADE_OK;
+}
+
+int cascade_batch_tune_next(cascade_batch_t* b, int32_t rounds, int32_t use_cache) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!b || rounds < 0) return CASCADE_ERR_INVALID_ARG;
+  b->tune_auto = rounds > 0;
+  if (rounds > 0) b->tune_rounds = rounds;
+  b->tune_use_cache = use_cache != 0;
+  b->tuned_key.clear();
+  b->tune_countdown = -1;
+  return CASCADE_OK;
+}
+
+int cascade_batch_tune_warmup(cascade_batch_t* b, int64_t steps) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!b || steps < 0) return CASCADE_ERR_INVALID_ARG;
+  b->tune_warmup = steps;
+  return CASCADE_OK;
+}
+
+int cascade_batch_tuning_report(cascade_batch_t* b, cascade_batch_variant* cands, double* ns_per_unit, int32_t max,
+                                int32_t* n_out) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!b || max < 0 || (max > 0 && (!cands || !ns_per_unit))) return CASCADE_ERR_INVALID_ARG;
+  const int n = (int)b->tune_cands.size() < max ? (int)b->tune_cands.size() : max;
+  for (int i = 0; i < n; ++i) {
+    cands[i] = b->tune_cands[i];
+    ns_per_unit[i] = b->tune_ns[i];
+  }
+  if (n_out) *n_out = n;
+  return CASCADE_OK;
 }
 
 int cascade_batch_poll(cascade_batch_t* b, int32_t* done_slots, int32_t max, int32_t* n_out, int32_t wait) {
   g_msg[0] = '\0';  // a message describes this call only
   if (!b || max < 0 || (max > 0 && !done_slots)) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(b->device);
-  int best = -1;
   if (wait) {
     // all queued work, then a fresh snapshot
     const int rc = batch_enqueue(b, 0);
     if (rc) return rc;
     const int k = (b->snap_next + kSnapRing - 1) % kSnapRing;
     CUDA_TRY(cudaEventSynchronize(b->ev_snap[k]));
-    best = k;
+    batch_harvest(b, k);
   } else {
     for (int k = 0; k < kSnapRing; ++k) {
       if (b->snap_seq[k] == 0) continue;
       const cudaError_t q = cudaEventQuery(b->ev_snap[k]);
       if (q == cudaErrorNotReady) continue;
       if (q != cudaSuccess) return cuda_fail(q, "cudaEventQuery");
-      if (best < 0 || b->snap_seq[k] > b->snap_seq[best]) best = k;
+      batch_harvest(b, k);
     }
   }
   int n = 0;
-  if (best >= 0) {
-    const long long seq = b->snap_seq[best];
+  if (b->landed_seq > 0) {
+    const long long seq = b->landed_seq;
     for (int i = 0; i < b->n_slots && n < max; ++i) {
       if (!b->members[i] || b->reported[i]) continue;
       // only snapshots queued after the member's admission speak for it
       if (seq <= b->admit_seq[i]) continue;
-      if (b->h_snap[best][i] == 0) {
+      if (b->landed[i] == 0) {
         done_slots[n++] = i;
         b->reported[i] = 1;
       }
@@ -1160,6 +1511,7 @@ int cascade_batch_release(cascade_batch_t* b, int32_t slot) {
   }
   cascade_t* h = b->members[slot];
   b->used -= h->bytes;
+  b->seed_particles -= 2LL * h->p.nx * h->p.ppc;
   b->members[slot] = nullptr;
   b->reported[slot] = 0;
   return cascade_destroy(h);

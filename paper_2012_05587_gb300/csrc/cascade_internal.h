@@ -83,6 +83,9 @@ struct Dev {
   long long* hole_a[2];// holes below the new count
   long long* hole_b[2];// live particles at or above the new count
   long long min_per_cta;  // particles per active CTA before another CTA is woken
+  int gauss_every;     // > 0: the step computes the Gauss residual every gauss_every steps
+  double* gauss_rho;   // its charge per node times dx (nx, kept zeroed between uses)
+  double* gauss_out;   // its result
 };
 
 // A batch of cascades advanced together (one launch per kernel per step).
@@ -117,16 +120,16 @@ void set_error_message(const char* msg);
   cudaError_t step_timed_##SUFFIX(const Dev& d, cudaStream_t s, cudaEvent_t before, cudaEvent_t after); \
   cudaError_t gauss_##SUFFIX(const Dev& d, double* rho_dx, double* out, cudaStream_t s);       \
   cudaError_t configure_##SUFFIX(Dev& d, int num_sms);                                         \
-  cudaError_t batch_configure_##SUFFIX(int max_nx, int fine, int num_sms, int* grid, int* block,   \
-                                       size_t* smem, int* dep);                                 \
+  cudaError_t batch_configure_##SUFFIX(int max_nx, int fine, int num_sms, int shape, int stage, int* grid, \
+                                       int* block, size_t* smem, int* dep);                     \
   cudaError_t batch_step_##SUFFIX(const BatchDev& b, int grid, int block, size_t smem, int dep,   \
                                   cudaStream_t s, cudaEvent_t before = nullptr,                 \
                                   cudaEvent_t after = nullptr);                                 \
   size_t partial_bytes_##SUFFIX();                                                             \
   cudaError_t histogram_##SUFFIX(const Dev& d, int sp, int quantity, int nbins, double lo, double hi,    \
                                  unsigned long long* out, cudaStream_t s);                           \
-  cudaError_t upload_##SUFFIX(const Dev& d, int sp, long long first, long long count, const double* off_src, \
-                              const double* u_src, unsigned int* bad, cudaStream_t s);
+  cudaError_t upload_##SUFFIX(const Dev& d, int sp, long long first, long long count, const void* off_src, \
+                              const void* u_src, int src_f32, unsigned int* bad, cudaStream_t s);
 
 CASCADE_DECLARE_LAUNCHERS(fp64)
 CASCADE_DECLARE_LAUNCHERS(fp32)

@@ -1392,9 +1392,9 @@ __global__ void __launch_bounds__(kFieldBlock) k_batch_field(BatchDev b) {
 // grid, offset in [0, 1), finite momentum) and the number of bad ones is
 // counted in *bad.
 // ---------------------------------------------------------------------------
-template <class Real>
-__global__ void k_upload(Dev d, int s, long long first, long long count, const double* off_src,
-                         const double* u_src, unsigned int* bad) {
+template <class Real, class Src>
+__global__ void k_upload(Dev d, int s, long long first, long long count, const Src* off_src,
+                         const Src* u_src, unsigned int* bad) {
   Real* off = static_cast<Real*>(d.off[s]) + first;
   Real* u = static_cast<Real*>(d.u[s]) + first;
   const int* cell = d.cell[s] + first;
@@ -1452,9 +1452,13 @@ __global__ void k_histogram(Dev d, int s, int quantity, int nbins, double lo, do
 // ---------------------------------------------------------------------------
 // Gauss's-law residual of the current state (diagnostic, not in the step).
 // ---------------------------------------------------------------------------
+// every > 0: part of a step -- only every every-th step computes (the step
+// counter lives on the device, so captured graphs keep the cadence); the
+// reduce kernel leaves rho_dx zeroed for the next use.  every = 0: on demand.
 template <class Real>
-__global__ void k_gauss_deposit(Dev d, double* rho_dx) {
+__global__ void k_gauss_deposit(Dev d, double* rho_dx, int every = 0) {
   Ctl* ctl = d.ctl;
+  if (every > 0 && ctl->step % every != 0) return;
   const long long N0 = ctl->n[0], N1 = ctl->n[1];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N0 + N1;
        t += (long long)gridDim.x * blockDim.x) {
@@ -1471,8 +1475,9 @@ __global__ void k_gauss_deposit(Dev d, double* rho_dx) {
 }
 
 template <class Real>
-__global__ void k_gauss_reduce(Dev d, const double* rho_dx, double* out) {
+__global__ void k_gauss_reduce(Dev d, double* rho_dx, double* out, int every = 0) {
   __shared__ double sh[128];
+  if (every > 0 && d.ctl->step % every != 0) return;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   // dE/dx = rho - rho_GJ (Eq. 25); with open boundaries interior nodes only
   for (int i = threadIdx.x + (d.open_bc ? 1 : 0); i < d.nx; i += blockDim.x) {
@@ -1480,6 +1485,10 @@ __global__ void k_gauss_reduce(Dev d, const double* rho_dx, double* out) {
     v[2] = fmax(v[2], fabs(d.E[i] - d.E[im] - (rho_dx[i] - d.rho_gj * d.dx)));
   }
   block_reduce4(v, sh);
+  if (every > 0) {
+    // every thread's reads of rho_dx are done (block_reduce4 synchronises)
+    for (int i = threadIdx.x; i < d.nx; i += blockDim.x) rho_dx[i] = 0.0;
+  }
   if (threadIdx.x == 0) {
     *out = v[2];
     const long long st = d.ctl->step;
@@ -1665,6 +1674,10 @@ struct Launchers {
     } else {
       k_field<Real, false><<<d.grid_field, kFieldBlock, 0, st>>>(d);
     }
+    if (d.gauss_every > 0) {  // the per-step Gauss residual, every gauss_every steps
+      k_gauss_deposit<Real><<<d.grid_push, 256, 0, st>>>(d, d.gauss_rho, d.gauss_every);
+      k_gauss_reduce<Real><<<1, 1024, 0, st>>>(d, d.gauss_rho, d.gauss_out, d.gauss_every);
+    }
     return cudaGetLastError();
   }
 
@@ -1699,25 +1712,23 @@ struct Launchers {
     }
   }
 
-  static cudaError_t batch_configure(int max_nx, int fine, int num_sms, int* grid, int* block, size_t* smem,
-                                     int* dep) {
+  // Launch configuration of the batched particle kernel for one variant:
+  // shape (see BatchShape) and stage (cp.async staging, FP32 only).  A stage
+  // request that does not fit beside E, the accumulator and the kernel's
+  // static shared memory (per CTA, and for the CTAs per SM of the shape, with
+  // the 1 KB the system reserves per CTA) returns cudaErrorInvalidValue, as
+  // does a grid too large for the shared-memory accumulator.
+  static cudaError_t batch_configure(int max_nx, int fine, int num_sms, int shape, int stage, int* grid, int* block,
+                                     size_t* smem, int* dep) {
     int dp = sizeof(Real) == 8 ? 0 : (fine ? 4 : 1);
     const size_t limit = 200 * 1024;
     if (smem_bytes(max_nx, kSmemESmemS, dp) > limit && dp == 4) dp = 1;
     const size_t sm = smem_bytes(max_nx, kSmemESmemS, dp);
     if (sm > limit) return cudaErrorInvalidValue;
-    // measured on the 256-cascade scan (3000 steps, FP32): shape 0 1.73e11,
-    // 1 1.69e11, 2 1.82e11, 3 1.87e11 particle-steps/s; the kernel keeps its
-    // member's descriptor in registers, so 64 registers spill
-    int shape = env_int("CASCADE_BATCH_SHAPE", 3);  // measurement override
-    if (shape < 0 || shape > 3) shape = 3;
+    if (shape < 0 || shape > 3) return cudaErrorInvalidValue;
+    if (stage && sizeof(Real) != 4) return cudaErrorInvalidValue;
     const int threads = batch_threads(shape);
-    // FP32: stage the particles through shared memory where the staging area
-    // fits beside E, the accumulator and the kernel's static shared memory
-    // (per CTA, and for the CTAs per SM of the launch shape, with the 1 KB
-    // the system reserves per CTA)
-    int stage = 0;
-    if (sizeof(Real) == 4 && env_int("CASCADE_BATCH_STAGE", 1) == 1) {
+    if (stage) {
       int dev = 0, optin = 0, per_sm_max = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1726,9 +1737,9 @@ struct Launchers {
       const cudaError_t ea = cudaFuncGetAttributes(&fa, batch_push_fn(dp, shape, true));
       if (ea != cudaSuccess) return ea;
       const size_t per_cta = sm + kStageBytesPerThread * threads;
-      if (per_cta + fa.sharedSizeBytes <= (size_t)optin &&
-          (per_cta + fa.sharedSizeBytes + 1024) * batch_minb(shape) <= (size_t)per_sm_max)
-        stage = 1;
+      if (per_cta + fa.sharedSizeBytes > (size_t)optin ||
+          (per_cta + fa.sharedSizeBytes + 1024) * batch_minb(shape) > (size_t)per_sm_max)
+        return cudaErrorInvalidValue;
     }
     const size_t smem_total = sm + (stage ? kStageBytesPerThread * threads : 0);
     const void* fn = batch_push_fn(dp, shape, stage != 0);
@@ -1741,7 +1752,7 @@ struct Launchers {
     *block = threads;
     *smem = smem_total;
     // kernel selector: accumulator form, launch shape, staging
-    *dep = dp + 16 * shape + 64 * stage;
+    *dep = dp + 16 * shape + 64 * (stage ? 1 : 0);
     return cudaSuccess;
   }
 
@@ -1762,12 +1773,18 @@ struct Launchers {
     return cudaGetLastError();
   }
 
-  static cudaError_t upload(const Dev& d, int sp, long long first, long long count, const double* off_src,
-                            const double* u_src, unsigned int* bad, cudaStream_t st) {
+  // src_f32: the staged offsets and momenta are float (else double)
+  static cudaError_t upload(const Dev& d, int sp, long long first, long long count, const void* off_src,
+                            const void* u_src, int src_f32, unsigned int* bad, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     long long blocks = (count + 255) / 256;
     if (blocks > 8192) blocks = 8192;
-    k_upload<Real><<<(int)blocks, 256, 0, st>>>(d, sp, first, count, off_src, u_src, bad);
+    if (src_f32)
+      k_upload<Real, float><<<(int)blocks, 256, 0, st>>>(d, sp, first, count, static_cast<const float*>(off_src),
+                                                         static_cast<const float*>(u_src), bad);
+    else
+      k_upload<Real, double><<<(int)blocks, 256, 0, st>>>(d, sp, first, count, static_cast<const double*>(off_src),
+                                                          static_cast<const double*>(u_src), bad);
     return cudaGetLastError();
   }
 
@@ -1808,9 +1825,9 @@ struct Launchers {
     return Launchers<REAL>::gauss(d, rho_dx, out, s);                                        \
   }                                                                                               \
   cudaError_t configure_##SUFFIX(Dev& d, int num_sms) { return Launchers<REAL>::configure(d, num_sms); } \
-  cudaError_t batch_configure_##SUFFIX(int max_nx, int fine, int num_sms, int* grid, int* block,   \
-                                       size_t* smem, int* dep) {                                \
-    return Launchers<REAL>::batch_configure(max_nx, fine, num_sms, grid, block, smem, dep);       \
+  cudaError_t batch_configure_##SUFFIX(int max_nx, int fine, int num_sms, int shape, int stage, int* grid, \
+                                       int* block, size_t* smem, int* dep) {                    \
+    return Launchers<REAL>::batch_configure(max_nx, fine, num_sms, shape, stage, grid, block, smem, dep); \
   }                                                                                               \
   cudaError_t batch_step_##SUFFIX(const BatchDev& b, int grid, int block, size_t smem, int dep,   \
                                   cudaStream_t s, cudaEvent_t before, cudaEvent_t after) {        \
@@ -1821,8 +1838,8 @@ struct Launchers {
                                  unsigned long long* out, cudaStream_t s) {                       \
     return Launchers<REAL>::histogram(d, sp, q, nb, lo, hi, out, s);                              \
   }                                                                                               \
-  cudaError_t upload_##SUFFIX(const Dev& d, int sp, long long first, long long count, const double* o, \
-                              const double* u, unsigned int* bad, cudaStream_t s) {               \
-    return Launchers<REAL>::upload(d, sp, first, count, o, u, bad, s);                            \
+  cudaError_t upload_##SUFFIX(const Dev& d, int sp, long long first, long long count, const void* o,  \
+                              const void* u, int src_f32, unsigned int* bad, cudaStream_t s) {      \
+    return Launchers<REAL>::upload(d, sp, first, count, o, u, src_f32, bad, s);                   \
   }                                         \
   }

@@ -33,6 +33,19 @@ def large_cascade(run: int = 0, precision: str = "fp32") -> dict:
                 steps=20000)
 
 
+def damping_cascade(run: int = 0, precision: str = "fp32", nx: int = 2048) -> dict:
+    """The f = 0.1 cascade whose oscillation Sections 5-6 follow through its
+    damping: Nx = 2048 (L = 41 c/omega_p), dx = 0.02, dt = 0.005, 4 + 4 seed
+    particles per cell, u ~ N(0, 0.01), E0 = 100, gamma_thr = 50,
+    eps_gamma = 5 (f = 0.1), in-place pairs (l_pp = 0), 10000 steps (t = 50):
+    the cascade screens the field at t = 1.6, the oscillation keeps its
+    amplitude for several periods, then the instability of Section 5 drives
+    secondary bursts once per period and the envelope decays (Eq. 24)."""
+    return dict(nx=nx, ppc=4, dx=0.02, dt=0.005, n0=1.0, u_spread=0.01, seed=seed_of(7, run), E0=100.0,
+                gamma_thr=50.0, eps_gamma=5.0, l_pp=0.0, particle_cap=nx * 4 * 400, precision=precision,
+                steps=10000, diag_ring=10000)
+
+
 def sweep_dt(E0: float, eps_gamma: float) -> float:
     """Time step of the precision sweep and the batch: resolve t_p = eps/E0 by 10."""
     return min(0.05, 0.1 * eps_gamma / E0)

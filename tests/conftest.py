@@ -11,6 +11,14 @@ if HERE not in sys.path:
     sys.path.insert(0, HERE)
 
 
+def pytest_sessionstart(session):
+    # the batch autotuner's cache: a file of the test session, not the user's
+    if "CASCADE_TUNE_CACHE" not in os.environ:
+        import tempfile
+
+        os.environ["CASCADE_TUNE_CACHE"] = os.path.join(tempfile.mkdtemp(prefix="cascade-tune-"), "tune.txt")
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built extension")
     config.addinivalue_line("markers", "slow: longer CPU runs")

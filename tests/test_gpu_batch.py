@@ -185,3 +185,97 @@ def test_fp32_batch_members_match_oracle_first_steps(precision):
             assert np.abs(E - E_ref).max() <= 5e-4 * scale, i
             assert np.abs(d["E_mean"] - d_ref["E_mean"]).max() <= 5e-4 * scale, i
             assert abs(d["n_pairs_total"][-1] - d_ref["n_pairs_total"][-1]) <= 0.02 * max(d_ref["n_pairs_total"][-1], 1)
+
+
+def test_fp32_request_admitted_mid_run_matches_running_alone():
+    """Continuous batching in FP32: a request admitted while two other
+    cascades are 50 steps into their runs gives the result it gives alone.
+    The batched kernel rounds its fixed-point current at a scale set by each
+    CTA's share of the batch, so the member alone and in the mix differ by
+    round-off, which the instability of Section 5 amplifies only late: the
+    first 100 steps agree to 1e-3 of max |E|, and the ensemble diagnostics
+    of the whole run (final pairs, screening time, peak field after
+    screening, oscillation period, final energy) to 2%."""
+    req = W.small_cascade(precision="fp32")
+    steps = req["steps"]
+    others = [dict(q, precision="fp32") for q in members_fp64()[1:]]
+    with CascadeBatch(slots=4, precision="fp32", max_nx=2048) as b:
+        b.admit(others[0], 1200)
+        b.admit(others[2], 1200)
+        b.run(50)
+        slot = b.admit(req, steps)
+        got = []
+        for _ in range(200):
+            b.run(16)
+            got += b.poll()
+            if slot in got:
+                break
+        assert slot in got
+        d_mix = b.diag(slot, steps)
+        assert b.counts(slot)["step"] == steps
+    with CascadeBatch([req]) as alone:
+        alone.step([steps])
+        d_alone = alone.diag(0, steps)
+    assert np.abs(d_mix["E_mean"][:100] - d_alone["E_mean"][:100]).max() <= 1e-3 * np.abs(d_alone["E_absmax"]).max()
+    e_mix, e_alone = _ens(d_mix), _ens(d_alone)
+    for k in ("pairs", "peak_after_screen", "period", "energy", "first_zero"):
+        assert e_mix[k] == pytest.approx(e_alone[k], rel=0.02), k
+
+
+def test_autotuned_scan_matches_oracle_and_caches_its_choice(tmp_path, monkeypatch):
+    """Autotuning of the batched particle kernel (the scan's launch shape is
+    picked by measurement).  The 256-cascade scan, armed to measure even on a
+    cache hit, runs its first steps cycling through every candidate variant
+    (four launch shapes, with and without cp.async staging), one step each,
+    then continues with the fastest.  Every step was computed by whichever
+    variant it drew, so the members' agreement with the FP64 oracle at step
+    60 covers all candidates.  The choice is stored under the batch's size
+    class, and a second batch of the same class takes it from the cache."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("CASCADE_TUNE_CACHE", str(cache))
+    scan = [dict(q) for q in W.batch_scan(256)]
+    for q in scan:
+        q.pop("steps")
+    steps = 60
+    order = sorted(range(len(scan)), key=lambda i: scan[i]["nx"] * scan[i]["ppc"])
+    picks = [order[0], order[len(order) // 2], order[-1]]
+    with CascadeBatch(scan) as b:
+        b.tune_next(rounds=4, use_cache=False)
+        b.step([steps] * len(scan))
+        v = b.variant()
+        assert v["source"] == "tuned" and v["ns_per_unit"] > 0, v
+        for i in picks:
+            p = scan[i]
+            E, _ = b.fields(i)
+            d = b.diag(i, steps)
+            ref = oracle.Oracle(T.oracle_params(p))
+            d_ref = ref.step(steps)
+            E_ref, _ = ref.fields()
+            scale = np.abs(E_ref).max()
+            assert np.abs(E - E_ref).max() <= 2e-4 * scale, i
+            for k in ("n_elec", "n_posi", "n_pairs_total"):
+                assert abs(d[k][-1] - d_ref[k][-1]) <= 0.01 * max(d_ref[k][-1], 1), (i, k)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].split("\t")[1] == f"{v['shape']} {v['stage']} {v['prefetch']} {v['member_cost']}"
+    with CascadeBatch(scan) as b2:
+        b2.step([16] * len(scan))
+        v2 = b2.variant()
+        assert v2["source"] == "cached"
+        assert (v2["shape"], v2["stage"], v2["prefetch"]) == (v["shape"], v["stage"], v["prefetch"])
+
+
+def test_forced_variant_and_tuning_off(monkeypatch):
+    """A forced variant (the measurement overrides) turns tuning off and is
+    used as given; one that does not fit the batch is rejected."""
+    p = W.small_cascade(precision="fp32")
+    with CascadeBatch([p]) as b:
+        b.set_variant(shape=1, stage=0, prefetch=2, member_cost=512)
+        b.step([32])
+        v = b.variant()
+        assert v["source"] == "forced" and (v["shape"], v["stage"], v["prefetch"], v["member_cost"]) == (1, 0, 2, 512)
+        with pytest.raises(CascadeError):
+            b.set_variant(shape=7, stage=0, prefetch=0)
+    monkeypatch.setenv("CASCADE_BATCH_SHAPE", "2")
+    with CascadeBatch([p]) as b:
+        b.step([32])
+        assert b.variant()["source"] == "forced" and b.variant()["shape"] == 2
