@@ -898,7 +898,7 @@ int batch_occupied(const cascade_batch_t* b) {
   return occ;
 }
 
-// Autotuning (spec pattern 2): the candidates -- the four launch shapes
+// Autotuning of the batch's launch shape: the candidates -- the four launch shapes
 // with the particles staged through shared memory (FP32) and without it,
 // then with an L2 prefetch one iteration ahead -- run in turn, one batch step
 // each, round after round, so that each is measured over the same stretch of
