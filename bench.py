@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--cap", type=int, default=0, help="particle cap per species (0 = the workload's)")
     ap.add_argument("--ppc", type=int, default=0, help="seed particles per cell per species (0 = the workload's)")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "batch", "serve", "sweep", "paper", "corotating", "damping"],
+                    choices=["large", "batch", "serve", "sweep", "paper", "corotating", "damping", "parity"],
                     help="large: one large cascade (default); batch: the 256-cascade parameter scan in one "
                          "launch per step; serve: Poisson arrivals admitted by footprint; sweep: FP32 vs FP64 "
                          "errors of the ensemble diagnostics")
@@ -94,10 +94,13 @@ def parse():
                     help="cascades run one at a time in FP64 for comparison, spread evenly over the predicted "
                          "particle-steps (0 = every scan member, or 64 requests when serving)")
     ap.add_argument("--paper-time", type=float, default=12.0, help="paper workload: simulated time (1/omega_p)")
+    ap.add_argument("--paper-fs", default="0.1,0.01,0.004", help="paper workload: values of f")
+    ap.add_argument("--paper-dt-factors", default="1", help="paper workload: multiples of the paper's time step")
     ap.add_argument("--save-series", default="", help="paper/corotating workloads: directory for the series")
     ap.add_argument("--corot-time", type=float, default=200.0, help="corotating workload: simulated time")
     ap.add_argument("--sweep-seeds", type=int, default=8, help="sweep workload: seeds averaged per configuration")
     ap.add_argument("--damping-seeds", type=int, default=32, help="damping workload: seeds per precision")
+    ap.add_argument("--parity-steps", type=int, default=800, help="parity workload: steps of the large cascade")
     ap.add_argument("--sweep-rows", default="", help="sweep workload: comma-separated configuration indices (all)")
     return ap.parse_args()
 
@@ -463,8 +466,9 @@ def timed_phase(c, nsteps, stream, bpp, peak, prec):
 
 def e2e_run(c, p, steps, stream, barrier):
     """Same workload through the public API with host buffers: upload the
-    state from pinned host memory (cascade_create_from_state), then every
-    step read its record back (cascade_diag), finally read E and J."""
+    state from pinned host memory (cascade_create_from_state, FP32 arrays
+    for an FP32 cascade), then every step read its record back
+    (cascade_diag), finally read E and J.  Closes c."""
     import torch
 
     from paper_2012_05587_gb300 import Cascade
@@ -491,6 +495,11 @@ def e2e_run(c, p, steps, stream, barrier):
     hE = pinned(len(E), torch.float64)
     hE[:] = E
     del part
+    # the bench's cascade is released first: its device memory returns to
+    # torch's caching allocator, which the new cascade then reuses, as a user
+    # running cascades one after another would (a first-ever allocation of the
+    # ~6 GB state adds about 60 ms of cudaMalloc to the upload)
+    c.close()
     barrier()
     t0 = time.perf_counter()
     c2 = Cascade(p, state={"elec": host[0], "posi": host[1], "E": hE})

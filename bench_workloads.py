@@ -335,6 +335,47 @@ def run_sweep(args) -> int:
     return 0
 
 
+def run_parity(args) -> int:
+    """The benchmark's own state in three precisions: the large cascade
+    (Nx = 16384, 64 + 64 per cell) through the cascade, screening and the
+    oscillation after it (--parity-steps, 800 by default: six periods) in
+    FP32-mixed, FP32-mixed-fine and FP64 on the GPU; per-cell ensemble
+    diagnostics of each and the relative error of the FP32 forms against
+    FP64.  (The comparison with the FP64 oracle, on a slice of the same
+    plasma, is tests/test_gpu_full_size.py.)"""
+    import torch
+
+    from paper_2012_05587_gb300 import Cascade, analysis as A, workloads as W
+
+    steps = args.parity_steps
+    out = {}
+    secs = {}
+    for prec in ("fp32", "fp32_fine", "fp64"):
+        p = W.large_cascade(precision=prec)
+        if prec == "fp64":
+            p["particle_cap"] = 200_000_000
+        p["diag_ring"] = max(4096, steps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with Cascade(p) as c:
+            c.step(steps)
+            rec = c.diag(steps)
+        torch.cuda.synchronize()
+        secs[prec] = time.perf_counter() - t0
+        e = A.ensemble(rec, p)
+        e["particles_per_cell"] = float((rec["n_elec"] + rec["n_posi"])[-1]) / p["nx"]
+        e["energy_per_cell"] = e.pop("final_energy") / p["nx"]
+        e["pairs_per_cell"] = e.pop("final_pairs") / p["nx"]
+        out[prec] = e
+    line = {"metric": B.METRIC, "value": None, "unit": UNIT,
+            "workload": f"large cascade (Nx = 16384, 64 + 64 per cell) for {steps} steps in three precisions",
+            "diagnostics": out, "seconds": secs,
+            "fp32_rel_err": A.relative_errors(out["fp32"], out["fp64"]),
+            "fp32_fine_rel_err": A.relative_errors(out["fp32_fine"], out["fp64"])}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_damping(args) -> int:
     """Damping of the large-amplitude oscillation (Sections 5-6, Eq. 24):
     the f = 0.1 cascade of workloads.damping_cascade over --damping-seeds
@@ -375,31 +416,19 @@ def run_damping(args) -> int:
     return 0
 
 
-def paper_scale_params(f: float, precision: str = "fp32") -> dict:
-    """Section 3 setup at the paper's own parameters: E0 = 10^3.5, L = 10^1.5
-    in N_L = 2000 cells, dt = 10^-3.5, gamma_thr = 500, one particle per cell
-    per species, in-place pair creation (l_pp = 0)."""
-    g = 500.0
-    eps = f * g
-    E0 = 10 ** 3.5
-    nx = 2000
-    pred = E0 * E0 * np.log(2 / f) / (2 * g)  # Eq. 5 screening density per species, in n0
-    return dict(nx=nx, ppc=1, dx=10 ** 1.5 / nx, dt=10 ** -3.5, n0=1.0, u_spread=0.0, seed=9000 + int(1e4 * f),
-                E0=E0, gamma_thr=g, eps_gamma=eps, l_pp=0.0, precision=precision,
-                particle_cap=int(1.5 * pred * nx) + 4096, diag_ring=1 << 16)
-
-
 def run_paper(args) -> int:
     """The paper-scale cascades of Section 3 (f = 0.1, 0.01, 0.004) against
     Eq. 3 (growth), Eq. 5 (density at screening), Eq. 10 (mean gamma) and
     Eq. 12 (oscillation frequency, with the measured n and <1/gamma^3>)."""
     import torch
 
-    from paper_2012_05587_gb300 import Cascade, analysis as A
+    from paper_2012_05587_gb300 import Cascade, analysis as A, workloads as W
 
     rows = []
-    for f in (0.1, 0.01, 0.004):
-        p = paper_scale_params(f, args.precision)
+    fs = [float(x) for x in args.paper_fs.split(",")]
+    factors = [float(x) for x in args.paper_dt_factors.split(",")]
+    for f, fac in [(f, fac) for f in fs for fac in factors]:
+        p = W.paper_scale(f, args.precision, dt_factor=fac)
         g, eps, E0 = p["gamma_thr"], p["eps_gamma"], p["E0"]
         ta = g / E0
         steps = int(args.paper_time / p["dt"])
@@ -445,7 +474,7 @@ def run_paper(args) -> int:
         ns = full["n_elec"][k_s] / (p["nx"] * p["ppc"])
         L = p["nx"] * p["dx"]
         row = {
-            "f": f, "steps": steps, "seconds": el,
+            "f": f, "dt": p["dt"], "dt_factor": fac, "steps": steps, "seconds": el,
             "particle_steps": float(N.sum()),
             "growth_rate_t_a": G * ta,
             "eq3_W_2_over_f": A.lambert_growth_rate(E0, g, eps) * ta,
@@ -517,4 +546,4 @@ def run_corotating(args) -> int:
 
 def run(args) -> int:
     return {"batch": run_batch, "serve": run_serve, "sweep": run_sweep, "paper": run_paper,
-            "corotating": run_corotating, "damping": run_damping}[args.workload](args)
+            "corotating": run_corotating, "damping": run_damping, "parity": run_parity}[args.workload](args)

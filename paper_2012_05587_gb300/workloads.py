@@ -46,6 +46,21 @@ def damping_cascade(run: int = 0, precision: str = "fp32", nx: int = 2048) -> di
                 steps=10000, diag_ring=10000)
 
 
+def paper_scale(f: float, precision: str = "fp32", dt_factor: float = 1.0) -> dict:
+    """Section 3 setup at the paper's own parameters: E0 = 10^3.5, L = 10^1.5
+    in N_L = 2000 cells, dt = 10^-3.5 (times dt_factor, for convergence
+    studies), gamma_thr = 500, eps_gamma = f gamma_thr, one particle per cell
+    per species at rest, in-place pair creation (l_pp = 0).  The particle
+    cap allows 1.5 times the density at screening of Eq. 5."""
+    g = 500.0
+    E0 = 10 ** 3.5
+    nx = 2000
+    pred = E0 * E0 * math.log(2 / f) / (2 * g)  # Eq. 5, per species, in n0
+    return dict(nx=nx, ppc=1, dx=10 ** 1.5 / nx, dt=10 ** -3.5 * dt_factor, n0=1.0, u_spread=0.0,
+                seed=9000 + int(1e4 * f), E0=E0, gamma_thr=g, eps_gamma=f * g, l_pp=0.0, precision=precision,
+                particle_cap=int(1.5 * pred * nx) + 4096, diag_ring=1 << 16)
+
+
 def sweep_dt(E0: float, eps_gamma: float) -> float:
     """Time step of the precision sweep and the batch: resolve t_p = eps/E0 by 10."""
     return min(0.05, 0.1 * eps_gamma / E0)
