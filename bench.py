@@ -19,6 +19,13 @@ qed_active the same metric and roofline on two timed phases in which the
            QED model works: the cascade itself (steps 0-200, the particle
            count growing from the seed to screening) and the secondary pair
            bursts that damp the oscillation (from step 1000)
+batch_scan the 256-cascade parameter scan for its first 300 steps in one
+           batch: its particle-steps/s and the batched particle kernel's
+           roofline (``--workload batch`` runs the full 3000 steps)
+serving    150 requests of the serving distribution arriving at 5 per second
+           (below capacity): aggregate particle-steps/s and p50/p99 time to
+           result (``--workload serve`` runs 2000 requests, saturated and
+           below capacity)
 cpu_baseline  the FP64 oracle on a bounded slice of the same workload
 
 ``--impl reference`` times the oracle (the only reference this method has)
@@ -74,6 +81,12 @@ def parse():
     ap.add_argument("--burst-start", type=int, default=1000,
                     help="large workload: step where the timed secondary-burst phase starts (0 = skip)")
     ap.add_argument("--burst-steps", type=int, default=100)
+    ap.add_argument("--serve-summary-requests", type=int, default=150,
+                    help="large workload: requests of the serving entry (0 = skip)")
+    ap.add_argument("--serve-summary-rate", type=float, default=5.0,
+                    help="large workload: arrival rate of the serving entry (requests/s)")
+    ap.add_argument("--batch-summary-steps", type=int, default=300,
+                    help="large workload: steps of the batched scan timed for the batch_scan entry (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cap", type=int, default=0, help="particle cap per species (0 = the workload's)")
@@ -385,6 +398,16 @@ def main():
         e2e = e2e_run(c, p, args.steps, stream, barrier)
     c.close()
 
+    batch = serving = None
+    if prec == "fp32" and args.batch_summary_steps > 0:
+        import bench_workloads
+
+        batch = bench_workloads.batch_scan_summary(args.batch_summary_steps)
+    if prec == "fp32" and args.serve_summary_requests > 0:
+        import bench_workloads
+
+        serving = bench_workloads.serve_summary(args.serve_summary_requests, args.serve_summary_rate)
+
     cpu = cpu_mc = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, psx, el, nt, sample = oracle_slice(150, 60)
@@ -412,6 +435,8 @@ def main():
                        "l2": "inputs larger than L2 (particle state >> 129 MB)"},
             "roofline": roof,
             "qed_active": {"cascade_phase": casc, "burst_phase": burst},
+            "batch_scan": batch,
+            "serving": serving,
             "cpu_baseline": cpu,
             "cpu_multicore": cpu_mc,
             "e2e": e2e,

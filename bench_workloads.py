@@ -128,6 +128,69 @@ def run_batch(args) -> int:
     return 0
 
 
+def batch_scan_summary(steps: int = 300, n: int = 256, prec: str = "fp32") -> dict:
+    """A short run of the batched scan for the default bench line: the n
+    cascades of the parameter scan for the first `steps` steps (the cascade
+    phase of most members), launched step by step with CUDA events around
+    every launch of the batched particle kernel (tuning, when the size class
+    is not cached, runs inside these steps).  Particle-steps/s over the whole
+    steps and the particle kernel's roofline (24 B per particle-step in FP32)."""
+    import torch
+
+    from paper_2012_05587_gb300 import CascadeBatch, capi, workloads as W
+
+    scan = W.batch_scan(n, precision=prec, steps=steps)
+    peak, peak_kind = B.measured_peak()
+    bpp = B.BYTES_PER_PARTICLE_STEP["fp64" if prec == "fp64" else "fp32"]
+    stream = torch.cuda.current_stream()
+    b = CascadeBatch(scan)
+    capi.cascade_batch_set_timing(b.b, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    b.step([steps] * len(scan))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    tim = capi.cascade_batch_timing(b.b)
+    variant = b.variant()
+    ps = sum(_psteps(b.diag(i, steps)) for i in range(len(scan)))
+    b.close()
+    push_s = tim["particle_kernel_ms"] / 1e3
+    achieved = bpp * ps / push_s / 1e9
+    return {"workload": f"batched parameter scan, {len(scan)} cascades, steps 0-{steps}, {prec}",
+            "value": ps / (ms / 1e3), "unit": UNIT, "particle_steps": ps, "ms": ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "kernel": "k_batch_push", "bytes_per_particle_step": bpp, "peak_source": peak_kind,
+                         "particle_kernel_share": push_s * 1e3 / ms},
+            "variant": variant, "kernels_launched": tim["kernels_launched"]}
+
+
+def serve_summary(requests: int = 150, rate: float = 5.0, prec: str = "fp32") -> dict:
+    """A short serving run for the default bench line: `requests` requests
+    of the serving distribution (batch-scan parameters, steps U[500, 5000])
+    arriving as a Poisson stream at `rate` per second -- about a third of
+    the capacity measured with the full serving workload, so the times to
+    result measure latency rather than queueing -- admitted by footprint and
+    run by continuous batching on a private stream."""
+    import torch
+
+    from paper_2012_05587_gb300 import workloads as W
+
+    reqs = W.serving_requests(requests, rate=rate, run=2, precision=prec)
+    budget = int(0.6 * torch.cuda.mem_get_info()[0])
+    prev = torch.cuda.current_stream()
+    torch.cuda.set_stream(torch.cuda.Stream())
+    try:
+        out = _serve(reqs, prec, budget)
+    finally:
+        torch.cuda.set_stream(prev)
+    out["workload"] = (f"serving: {requests} requests of the serving distribution, Poisson arrivals at {rate}/s, "
+                       "admission by predicted device footprint, continuous batching")
+    out["unit"] = UNIT
+    return out
+
+
 def _batch_roofline(scan: list, steps: int, prec: str) -> dict:
     """The same scan again, launched step by step with CUDA events around
     every launch of the batched particle kernel: its algorithmic traffic
@@ -434,13 +497,17 @@ def run_paper(args) -> int:
         steps = int(args.paper_time / p["dt"])
         t0 = time.perf_counter()
         with Cascade(p) as c:
-            # run to the first zero of <E> (screening), chunk by chunk
+            # run to the first zero of <E> (screening), in chunks of a fixed
+            # simulated time (0.016, 50 steps at the paper's dt), so that the
+            # distribution below is sampled at the same time after screening
+            # whatever the time step
+            chunk = max(1, int(round(0.016 / p["dt"])))
             done = 0
             recs = []
             while done < steps:
-                c.step(500)
-                done += 500
-                r = c.diag(500)
+                c.step(chunk)
+                done += chunk
+                r = c.diag(chunk)
                 recs.append(r)
                 if (r["E_mean"] <= 0).any():
                     break

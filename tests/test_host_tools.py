@@ -79,3 +79,42 @@ def test_reference_arm_prints_the_contract_line():
     assert line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_damping_rate_of_a_damped_oscillation():
+    """Eq. 24's envelope: a cosine whose amplitude holds for 5 time units and
+    then decays as exp(-0.08 t); the fit over the peaks between 0.9 and 0.4
+    of the first peak recovers the rate, and an undamped cosine gives zero."""
+    t = np.linspace(0.0, 60.0, 60001)
+    env = np.where(t < 5.0, 1.0, np.exp(-0.08 * (t - 5.0)))
+    lam, n = A.damping_rate(t, 40.0 * env * np.cos(3.0 * t + 0.2))
+    assert lam == pytest.approx(0.08, rel=0.02) and n >= 5
+    lam0, _ = A.damping_rate(t, 40.0 * np.cos(3.0 * t + 0.2))
+    assert abs(lam0) < 1e-4
+
+
+def test_growth_rate_between_counts():
+    """The rate between two fixed counts of an exponential, whatever the
+    sampling, and the window of the parameters (Eq. 5 multiplicity)."""
+    t = np.linspace(0.0, 3.0, 301)
+    n = 1000.0 * np.exp(2.5 * t)
+    assert A.growth_rate_between(t, n, 4000.0, 400000.0) == pytest.approx(2.5, rel=1e-4)
+    p = dict(nx=256, ppc=4, n0=1.0, E0=100.0, gamma_thr=50.0, eps_gamma=5.0)
+    lo, hi = A.growth_window(p)
+    n_seed = 2 * 256 * 4
+    assert lo == 4 * n_seed and hi == pytest.approx(n_seed * A.screening_density(100.0, 50.0, 5.0) / 4)
+    assert A.growth_window(dict(p, E0=10.0, gamma_thr=20.0, eps_gamma=10.0)) is None  # one generation only
+    # the seed average of ln N: two runs growing at 2.0 and 3.0 with the same
+    # start average to 2.5 between the counts
+    recs = [{"t": t, "n_elec": 500.0 * np.exp(r * t), "n_posi": 500.0 * np.exp(r * t)} for r in (2.0, 3.0)]
+    assert A.seed_averaged_growth_rate(recs, (4000.0, 400000.0)) == pytest.approx(2.5, rel=1e-3)
+
+
+def test_paired_comparison_reports_bias_and_its_error():
+    rng = np.random.default_rng(0)
+    base = rng.normal(1.0, 0.2, 400)
+    refs = [{"x": v, "seed": i} for i, v in enumerate(base)]
+    runs = [{"x": v * 1.03 + rng.normal(0.0, 0.01), "seed": i} for i, v in enumerate(base)]
+    c = A.paired_comparison(runs, refs)["x"]
+    assert c["rel_err"] == pytest.approx(0.03, abs=0.003)
+    assert 0.0 < c["rel_se"] < 0.002 and c["n"] == 400
