@@ -287,7 +287,11 @@ int cascade_batch_info(cascade_batch_t* b, int32_t* slots, int32_t* occupied, si
  * scale of each CTA's share of the batch. */
 typedef struct {
   int32_t shape;        /* threads per CTA and register budget: 0 = 2 x 512 threads (64
-                           registers), 1 = 512 (128), 2 = 768 (80), 3 = 640 (96) */
+                           registers), 1 = 512 (128), 2 = 768 (80), 3 = 640 (96), all
+                           persistent with the members' work split evenly over the CTAs;
+                           4 = 1024 (64), a row of CTAs per member (grid members x CTAs,
+                           each member's descriptor in the constant bank; FP32 batches that
+                           hold a slice of the member table; the FP32 default) */
   int32_t stage;        /* 1: particles staged through shared memory with cp.async (FP32) */
   int32_t prefetch;     /* iterations ahead each warp prefetches its particles into L2 (0..8) */
   int32_t member_cost;  /* fixed work units per member in the partition (4-particle chunks) */
@@ -304,15 +308,16 @@ enum { CASCADE_VARIANT_DEFAULT = 0, CASCADE_VARIANT_CACHED = 1, CASCADE_VARIANT_
  * to another class.  It first looks the class up in the per-device cache
  * file (cascade_tune_cache_path); on a miss, after a warm-up
  * (cascade_batch_tune_warmup), it runs the
- * candidate variants -- the four shapes with cp.async staging (FP32) and
- * without it (then an L2 prefetch) -- one batch step each, round after round
+ * candidate variants -- the five shapes (four in FP64) with cp.async staging
+ * (FP32) and without it (then an L2 prefetch) -- one batch step each, round after round
  * (4 rounds, or as many as the call's steps allow), times the particle
  * kernel with CUDA events, scores each variant by time per work unit of the
  * partition, keeps the fastest and stores it in the cache.  Tuning steps are
  * real steps of the members' work.  Setting any of CASCADE_BATCH_SHAPE,
  * CASCADE_BATCH_STAGE, CASCADE_BATCH_PREFETCH, CASCADE_BATCH_MEMBER_COST
  * before creation forces a variant (no tuning); CASCADE_BATCH_TUNE=0 keeps
- * the default variant.
+ * the default variant.  CASCADE_BATCH_CTAS_PER_SM (1..64, default 8) sets how
+ * many CTAs per SM and step shape 4 splits the members' work into.
  *   cascade_batch_set_variant  forces v (CASCADE_ERR_INVALID_ARG if it does not
  *                              fit this batch) and disarms tuning
  *   cascade_batch_get_variant  the variant in use, where it came from

@@ -772,6 +772,61 @@ namespace {
 
 constexpr int kSnapRing = 4;  // remaining-count snapshots in flight
 
+// Slices of the constant-bank member table (one table per precision's
+// kernel translation unit; a batch holds one slice of n_slots entries for its
+// life).  First fit; -1 when no run of n free entries is left, and the batch
+// then has only the shared-memory kernel.
+std::mutex g_const_mu;
+std::vector<char> g_const_used[2];
+
+int const_slice_alloc(int precision, int n) {
+  std::lock_guard<std::mutex> lk(g_const_mu);
+  std::vector<char>& used = g_const_used[precision == CASCADE_FP64 ? 0 : 1];
+  if (used.empty()) used.assign(kConstMembers, 0);
+  for (int base = 0; base + n <= kConstMembers; ++base) {
+    int k = 0;
+    while (k < n && !used[base + k]) ++k;
+    if (k == n) {
+      for (int i = 0; i < n; ++i) used[base + i] = 1;
+      return base;
+    }
+    base += k;
+  }
+  return -1;
+}
+
+void const_slice_free(int precision, int base, int n) {
+  if (base < 0) return;
+  std::lock_guard<std::mutex> lk(g_const_mu);
+  std::vector<char>& used = g_const_used[precision == CASCADE_FP64 ? 0 : 1];
+  for (int i = 0; i < n && base + i < (int)used.size(); ++i) used[base + i] = 0;
+}
+
+BatchMember member_of(const Dev& d) {
+  BatchMember m{};
+  for (int s = 0; s < 2; ++s) {
+    m.cell[s] = d.cell[s];
+    m.off[s] = d.off[s];
+    m.u[s] = d.u[s];
+  }
+  m.ph_cell = d.ph_cell;
+  m.ph_off = d.ph_off;
+  m.E = d.E;
+  m.S_glob = d.S_glob;
+  m.uk_part = d.uk_part;
+  m.ctl = d.ctl;
+  m.cap4 = d.cap4;
+  m.ph_cap = d.ph_cap;
+  m.dt = d.dt;
+  m.dtdx = d.dtdx;
+  m.gamma_thr = d.gamma_thr;
+  m.eps_gamma = d.eps_gamma;
+  m.lpp_frac = d.lpp_frac;
+  m.nx = d.nx;
+  m.lpp_int = d.lpp_int;
+  return m;
+}
+
 }  // namespace
 
 struct cascade_batch {
@@ -829,6 +884,10 @@ struct cascade_batch {
   std::vector<double> tune_ns;                    // ... and their ns per work unit
   long long* d_units = nullptr;        // work units of each tuning step (device)
   long long seed_particles = 0;        // seed particles of the members (size class of the batch)
+  // constant-bank kernel (launch shape 4): the batch's slice of the member table
+  int const_base = -1;
+  BatchMember* h_members = nullptr;    // pinned staging of the table entries
+  int* d_member_ctas = nullptr;
 
   cudaError_t launch_step() {
     cudaEvent_t before = nullptr, after = nullptr;
@@ -852,14 +911,16 @@ struct cascade_batch {
 namespace {
 
 constexpr int kTuneMaxSteps = 256;  // tuning steps logged per tuning pass
+constexpr int kConstCtasPerSm = 8;  // constant-bank batch kernel: working CTAs per SM and step (4: 2.15e11, 8: 2.24e11, 16: 2.24e11 on the 256-cascade scan)
 
 // Launch parameters of one variant (no graph change); CASCADE_ERR_INVALID_ARG
 // when the variant does not fit this batch (staging beside a large grid, a
 // form the precision has no kernel for).
 int batch_config_variant(cascade_batch_t* b, const cascade_batch_variant& v) {
-  if (v.shape < 0 || v.shape > 3 || (v.stage != 0 && v.stage != 1) || v.prefetch < 0 || v.prefetch > 8 ||
+  if (v.shape < 0 || v.shape > 4 || (v.stage != 0 && v.stage != 1) || v.prefetch < 0 || v.prefetch > 8 ||
       v.member_cost < 0)
     return CASCADE_ERR_INVALID_ARG;
+  if (v.shape == 4 && b->const_base < 0) return CASCADE_ERR_INVALID_ARG;  // no slice of the member table
   const int fine = b->precision == CASCADE_FP32_MIXED_FINE ? 1 : 0;
   int grid = 0, block = 0, dep = 0;
   size_t smem = 0;
@@ -933,7 +994,7 @@ int batch_tune(cascade_batch_t* b, long long max_steps, long long* used) {
   if (b->tune_countdown > 0) return CASCADE_OK;
   std::vector<cascade_batch_variant> cand;
   for (int stage = 1; stage >= 0; --stage)
-    for (int shape : {3, 2, 1, 0}) {
+    for (int shape : {4, 3, 2, 1, 0}) {
       const cascade_batch_variant v{shape, stage, stage ? 0 : 1, 1024};
       if (batch_config_variant(b, v) == CASCADE_OK) cand.push_back(v);
     }
@@ -1140,13 +1201,22 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGetDevice"));
   e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
-  // default variant: 640 threads at 96 registers, the particles staged
-  // through shared memory where that fits (FP32), else an L2 prefetch one
-  // iteration ahead (measured best on the 256-cascade scan)
+  // a slice of the constant-bank member table (FP32 batches), needed before
+  // any variant of launch shape 4 can be configured
+  if (precision != CASCADE_FP64) b->const_base = const_slice_alloc(precision, max_slots);
+  // default variant, the best measured on the 256-cascade scan: the
+  // constant-bank kernel (FP32 with a slice of the member table) with the
+  // particles staged through shared memory, else the persistent kernel at
+  // 640 threads and 96 registers; staged where that fits, else with an L2
+  // prefetch one iteration ahead
   {
     const int st = precision == CASCADE_FP64 ? 0 : 1;
-    cascade_batch_variant v{3, st, st ? 0 : 1, 1024};
+    cascade_batch_variant v{b->const_base >= 0 ? 4 : 3, st, st ? 0 : 1, 1024};
     int rc = batch_config_variant(b, v);
+    if (rc == CASCADE_ERR_INVALID_ARG && v.shape == 4) {
+      v.shape = 3;
+      rc = batch_config_variant(b, v);
+    }
     if (rc == CASCADE_ERR_INVALID_ARG && v.stage) {
       v.stage = 0;
       v.prefetch = 1;
@@ -1191,7 +1261,8 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
   const size_t b_rem = (sizeof(long long) * n + 255) & ~size_t(255);
   const size_t b_items = (sizeof(long long) * (n + 1) + 255) & ~size_t(255);
   const size_t b_units = sizeof(long long) * kTuneMaxSteps;
-  const size_t total = b_devs + b_rem + b_items + b_units;
+  const size_t b_ctas = (sizeof(int) * n + 255) & ~size_t(255);
+  const size_t total = b_devs + b_rem + b_items + b_units + b_ctas;
   e = cudaMalloc(&b->d_block, total);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc batch tables"));
   char* base = static_cast<char*>(b->d_block);
@@ -1199,6 +1270,7 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
   b->d_remaining = reinterpret_cast<long long*>(base + b_devs);
   b->d_item_start = reinterpret_cast<long long*>(base + b_devs + b_rem);
   b->d_units = reinterpret_cast<long long*>(base + b_devs + b_rem + b_items);
+  b->d_member_ctas = reinterpret_cast<int*>(base + b_devs + b_rem + b_items + b_units);
   if ((e = cudaMemsetAsync(b->d_block, 0, total, b->stream)) != cudaSuccess) return fail(cuda_fail(e, "memset"));
   if ((e = cudaMallocHost(&b->h_devs, sizeof(Dev) * n)) != cudaSuccess) return fail(cuda_fail(e, "host mirror"));
   memset(b->h_devs, 0, sizeof(Dev) * n);
@@ -1220,6 +1292,23 @@ int cascade_batch_create_slots(int32_t max_slots, int32_t precision, int32_t max
   b->bd.max_nx = max_nx;
   b->bd.prefetch = b->var.prefetch;
   b->bd.member_cost = b->var.member_cost;
+  if (b->const_base >= 0) {
+    // the constant-bank kernel: the per-member CTA counts the plan kernel
+    // writes, cps waves of CTAs per step (CASCADE_BATCH_CTAS_PER_SM, a
+    // measurement override), and a row long enough for the members' shares
+    // (one member alone gets two rows' worth of SMs)
+    if ((e = cudaMallocHost(&b->h_members, sizeof(BatchMember) * n)) != cudaSuccess)
+      return fail(cuda_fail(e, "host member table"));
+    memset(b->h_members, 0, sizeof(BatchMember) * n);
+    const char* ev = getenv("CASCADE_BATCH_CTAS_PER_SM");
+    int cps = (ev && *ev) ? atoi(ev) : kConstCtasPerSm;
+    cps = cps < 1 ? 1 : (cps > 64 ? 64 : cps);
+    b->bd.member_ctas = b->d_member_ctas;
+    b->bd.const_base = b->const_base;
+    b->bd.target_ctas = cps * b->num_sms;
+    const int row = (2 * cps * b->num_sms + max_slots - 1) / max_slots;
+    b->bd.max_ctas = row > 8 * cps ? row : 8 * cps;
+  }
   if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return fail(cuda_fail(e, "sync"));
   *out = b;
   return CASCADE_OK;
@@ -1276,6 +1365,12 @@ int cascade_batch_admit(cascade_batch_t* b, const cascade_params* params, int32_
   b->h_devs[slot] = h->d;
   b->h_set[slot] = nsteps;
   CUDA_TRY(cudaMemcpyAsync(b->d_devs + slot, b->h_devs + slot, sizeof(Dev), cudaMemcpyHostToDevice, b->stream));
+  if (b->const_base >= 0) {
+    // the slot's entry of the constant-bank member table, behind the steps
+    // queued before it (none of them reads this slot: it was free)
+    b->h_members[slot] = member_of(h->d);
+    CUDA_TRY(batch_member_set_fp32(b->const_base + slot, b->h_members + slot, b->stream));
+  }
   CUDA_TRY(cudaMemcpyAsync(b->d_remaining + slot, b->h_set + slot, sizeof(long long), cudaMemcpyHostToDevice,
                            b->stream));
   if (slot_out) *slot_out = slot;
@@ -1571,6 +1666,8 @@ int cascade_batch_destroy(cascade_batch_t* b) {
   }
   if (b->ev_init) cudaEventDestroy(b->ev_init);
   for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
+  const_slice_free(b->precision, b->const_base, b->n_slots);
+  if (b->h_members) cudaFreeHost(b->h_members);
   if (b->h_devs) cudaFreeHost(b->h_devs);
   if (b->h_set) cudaFreeHost(b->h_set);
   if (b->d_block) cudaFree(b->d_block);

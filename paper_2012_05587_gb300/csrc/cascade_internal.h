@@ -88,6 +88,28 @@ struct Dev {
   double* gauss_out;   // its result
 };
 
+// The part of a member's descriptor that the constant-bank batch kernel
+// reads (k_batch_push_c): a table of these lives in __constant__ memory,
+// indexed by blockIdx.y, so every field is a warp-uniform constant-bank
+// operand instead of a per-thread register.
+struct BatchMember {
+  int32_t* cell[2];
+  void* off[2];
+  void* u[2];
+  int32_t* ph_cell;
+  void* ph_off;
+  double* E;
+  double* S_glob;
+  double* uk_part;
+  Ctl* ctl;
+  long long cap4, ph_cap;
+  double dt, dtdx, gamma_thr, eps_gamma, lpp_frac;
+  int nx, lpp_int;
+};
+
+// Entries of the constant-bank member table in each kernel translation unit.
+constexpr int kConstMembers = 64 * 1024 / sizeof(BatchMember) - 8;
+
 // A batch of cascades advanced together (one launch per kernel per step).
 struct BatchDev {
   const Dev* devs;               // [n] member descriptors
@@ -97,6 +119,10 @@ struct BatchDev {
   int max_nx;                    // largest member grid (shared-memory sizing)
   int prefetch;                  // iterations ahead the particle kernel prefetches into L2
   long long member_cost;         // fixed cost of a member in the partition, in 4-particle chunks
+  int* member_ctas;              // [n] constant-bank kernel: CTAs that work on each member this step
+  int const_base;                // constant-bank kernel: the batch's first entry in the member table
+  int target_ctas;               // constant-bank kernel: working CTAs the plan aims at per step
+  int max_ctas;                  // constant-bank kernel: CTAs launched per member (grid x)
 };
 
 enum PushVariant {
@@ -126,6 +152,7 @@ void set_error_message(const char* msg);
                                   cudaStream_t s, cudaEvent_t before = nullptr,                 \
                                   cudaEvent_t after = nullptr);                                 \
   size_t partial_bytes_##SUFFIX();                                                             \
+  cudaError_t batch_member_set_##SUFFIX(int index, const BatchMember* m, cudaStream_t s);       \
   cudaError_t histogram_##SUFFIX(const Dev& d, int sp, int quantity, int nbins, double lo, double hi,    \
                                  unsigned long long* out, cudaStream_t s);                           \
   cudaError_t upload_##SUFFIX(const Dev& d, int sp, long long first, long long count, const void* off_src, \

@@ -296,8 +296,10 @@ __device__ __forceinline__ void set_scales(PushState<Real, DEP>& st, double pcou
 // round-to-nearest intrinsics so that no operation is contracted), so pushes
 // far below the spacing of u still accumulate; the threshold test and the
 // recoil of a lepton near or above gamma_thr use the pair's sum in FP64.
-template <class Real, int V, int DEP, bool FAST, bool OPEN, bool STG = false, bool COMP = false>
-__device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP>& st, int s, long long base,
+// DevT: the cascade's descriptor -- Dev (the single-cascade kernel's kernel
+// parameter) or BatchMember (a batch member's entry in the constant bank).
+template <class Real, int V, int DEP, bool FAST, bool OPEN, bool STG = false, bool COMP = false, class DevT = Dev>
+__device__ __forceinline__ Real process4(const DevT& d, const PushState<Real, DEP>& st, int s, long long base,
                                          int cnt, int lane, const unsigned char* const* stg = nullptr) {
   static_assert(!COMP || (sizeof(Real) == 4 && !STG), "two-word momenta: FP32, direct loads");
   typedef typename AccOf<Real, DEP>::type Acc;
@@ -311,8 +313,9 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
   int cl[4] = {0, 0, 0, 0};
   Real of[4] = {zero, zero, zero, zero}, uu[4] = {zero, zero, zero, zero};
   float ul[4] = {0.f, 0.f, 0.f, 0.f};
-  float* ulp = COMP ? d.ulo[s] + base : nullptr;
-  if (COMP) {
+  float* ulp = nullptr;
+  if constexpr (COMP) {
+    ulp = d.ulo[s] + base;
     if (cnt == 4) {
       ld4(ulp, ul);
     } else {
@@ -484,7 +487,7 @@ __device__ __forceinline__ Real process4(const Dev& d, const PushState<Real, DEP
 
   // QED (Section 2): threshold emission with recoil; photons appended with
   // one warp-wide scan and one global atomic per slot that has emitters
-  if (OPEN) {
+  if constexpr (OPEN) {
     // departed particles: their indices join their species' hole list (a
     // warp can hold both species, so one warp-wide scan and one atomic per
     // species present)
@@ -1146,6 +1149,7 @@ __device__ __forceinline__ long long batch_units(const BatchDev& b, const Dev& d
 template <class Real>
 __global__ void __launch_bounds__(1024) k_batch_plan(BatchDev b) {
   __shared__ long long warp_tot[32];
+  __shared__ long long s_total;
   const int per = (b.n + blockDim.x - 1) / blockDim.x;
   const int lo = threadIdx.x * per;
   const int hi = min(lo + per, b.n);
@@ -1178,17 +1182,39 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchDev b) {
     b.item_start[i] = start;
     if (b.remaining[i] > 0) start += batch_units(b, b.devs[i]);
   }
-  if (threadIdx.x == blockDim.x - 1) b.item_start[b.n] = warp_tot[warp] + incl;
+  if (threadIdx.x == blockDim.x - 1) {
+    b.item_start[b.n] = warp_tot[warp] + incl;
+    s_total = warp_tot[warp] + incl;
+  }
+  if (b.member_ctas) {
+    // constant-bank kernel: each member's CTAs in proportion to its work
+    // units (rounded up), at least one, at most the grid's row
+    __syncthreads();
+    const long long total = s_total;
+    for (int i = lo; i < hi; ++i) {
+      int k = 0;
+      if (b.remaining[i] > 0 && total > 0) {
+        const long long u = batch_units(b, b.devs[i]);
+        const long long kk = (u * (long long)b.target_ctas + total - 1) / total;
+        k = kk < 1 ? 1 : (kk > b.max_ctas ? b.max_ctas : (int)kk);
+      }
+      b.member_ctas[i] = k;
+    }
+  }
 }
 
 // Chunks [a, e) of member `slot` (species 0's chunks first, then species
 // 1's), clipped to the member's chunk count: copy its descriptor, stage its E
 // and clear the accumulator, advance the particles, then add the CTA's sum of
 // gamma and current to the member's FP64 totals with global atomics.
+template <class Real, int DEP, bool STG, class DevT>
+__device__ __forceinline__ void batch_member_range(const BatchDev& b, const DevT& d, PushState<Real, DEP>& st,
+                                                   double* red, unsigned char* stage, long long a, long long e,
+                                                   long long C0, long long N0, long long N1);
+
 template <class Real, int DEP, bool STG>
 __device__ __forceinline__ void batch_range(const BatchDev& b, Dev& sd, PushState<Real, DEP>& st, double* red,
                                             unsigned char* stage, int slot, long long a, long long e) {
-  typedef typename AccOf<Real, DEP>::type Acc;
   {
     const long long* src = reinterpret_cast<const long long*>(b.devs + slot);
     long long* dst = reinterpret_cast<long long*>(&sd);
@@ -1205,6 +1231,19 @@ __device__ __forceinline__ void batch_range(const BatchDev& b, Dev& sd, PushStat
     __syncthreads();  // every thread has read sd before the next member overwrites it
     return;
   }
+  batch_member_range<Real, DEP, STG>(b, d, st, red, stage, a, e, C0, N0, N1);
+}
+
+// The particles of chunks [a, e) of one member (descriptor d: in shared
+// memory for k_batch_push, in the constant bank for k_batch_push_c): stage
+// its E and clear the accumulator, advance the particles, then add the CTA's
+// sum of gamma and current to the member's FP64 totals with global atomics.
+template <class Real, int DEP, bool STG, class DevT>
+__device__ __forceinline__ void batch_member_range(const BatchDev& b, const DevT& d, PushState<Real, DEP>& st,
+                                                   double* red, unsigned char* stage, long long a, long long e,
+                                                   long long C0, long long N0, long long N1) {
+  typedef typename AccOf<Real, DEP>::type Acc;
+  Ctl* ctl = d.ctl;
   const int nx = d.nx;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     st.Es[i] = (Real)d.E[i];
@@ -1268,9 +1307,10 @@ __device__ __forceinline__ void batch_range(const BatchDev& b, Dev& sd, PushStat
       cp_async_wait_prev();  // iteration it's copies have landed
       const int bb = (int)(it & 1);
       const unsigned char* stg[3] = {slot_of(bb, 0), slot_of(bb, 1), slot_of(bb, 2)};
-      gsum += (double)process4<Real, kSmemESmemS, DEP, true, false, true>(d, st, s, base, cnt, lane, stg);
+      gsum += (double)process4<Real, kSmemESmemS, DEP, true, false, true, false, DevT>(d, st, s, base, cnt, lane,
+                                                                                    stg);
     } else {
-      gsum += (double)process4<Real, kSmemESmemS, DEP, true, false>(d, st, s, base, cnt, lane);
+      gsum += (double)process4<Real, kSmemESmemS, DEP, true, false, false, false, DevT>(d, st, s, base, cnt, lane);
     }
   }
 #pragma unroll
@@ -1355,6 +1395,46 @@ __global__ void __launch_bounds__(BatchShape<SHAPE>::threads, BatchShape<SHAPE>:
     if (s1 <= s0 || s1 <= lo) continue;  // idle member, or one that ends before this range
     batch_range<Real, DEP, STG>(b, sd, st, red, stage, m, (lo > s0 ? lo : s0) - s0, (hi < s1 ? hi : s1) - s0);
   }
+}
+
+// The member table of the constant-bank batch kernel (each batch owns a
+// slice of it, from b.const_base).
+__constant__ BatchMember c_members[kConstMembers];
+
+// Constant-bank form of the batched particle kernel: grid (max_ctas, slots)
+// of 1024-thread CTAs.  CTA (x, m) works on member m only, on the x-th of the
+// member_ctas[m] equal parts of its chunks (the plan kernel sizes
+// member_ctas[m] in proportion to the member's work); the other CTAs of the
+// row return at once.  The member index is blockIdx.y, so its descriptor is
+// read from the constant bank with a warp-uniform index and needs no
+// per-thread registers: the kernel fits 1024 threads at 64 registers, like
+// the single-cascade kernel, where the shared-memory descriptor of
+// k_batch_push needs 96.  The hardware schedules the CTAs as SMs free up,
+// which balances the members.
+template <class Real, int DEP, bool STG>
+__global__ void __launch_bounds__(1024, 1) k_batch_push_c(BatchDev b) {
+  static_assert(!STG || sizeof(Real) == 4, "the staging slots hold four 4-byte values");
+  const int slot = blockIdx.y;
+  if (b.remaining[slot] <= 0) return;
+  const int K = b.member_ctas[slot];
+  if ((int)blockIdx.x >= K) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  const BatchMember& d = c_members[b.const_base + slot];
+  Ctl* ctl = d.ctl;
+  const long long cc = ctl->conv_count;
+  const long long N0 = ctl->n[0] + cc, N1 = ctl->n[1] + cc;
+  const long long C0 = (N0 + 3) >> 2, C = C0 + ((N1 + 3) >> 2);
+  const long long a = C * blockIdx.x / K, e = C * (blockIdx.x + 1) / K;
+  if (a >= e) return;  // the whole CTA returns together
+  typedef typename AccOf<Real, DEP>::type Acc;
+  const size_t eb = ((size_t)b.max_nx * sizeof(Real) + 15) & ~size_t(15);
+  PushState<Real, DEP> st;
+  st.Es = reinterpret_cast<Real*>(smem_raw);
+  st.Ss = reinterpret_cast<Acc*>(smem_raw + eb);
+  st.Ls = reinterpret_cast<int*>(smem_raw + 2 * eb);
+  unsigned char* stage = smem_raw + (DEP == 4 ? 3 : 2) * eb;
+  batch_member_range<Real, DEP, STG>(b, d, st, red, stage, a, e, C0, N0, N1);
 }
 
 template <class Real>
@@ -1691,11 +1771,21 @@ struct Launchers {
     }
   }
 
-  // shape: see BatchShape; stage: cp.async staging (FP32 only)
+  // shape: see BatchShape (0-3, the persistent kernel) or 4 (the
+  // constant-bank kernel k_batch_push_c, FP32 only); stage: cp.async staging
+  // (FP32 only).  nullptr: no such kernel.
   static const void* batch_push_fn(int dep, int shape, bool stage) {
     if constexpr (sizeof(Real) == 8) {
+      if (shape == 4) return nullptr;
       return batch_push_shape<0, false>(shape);
     } else {
+      if (shape == 4) {
+        if (stage)
+          return dep == 4 ? reinterpret_cast<const void*>(&k_batch_push_c<Real, 4, true>)
+                          : reinterpret_cast<const void*>(&k_batch_push_c<Real, 1, true>);
+        return dep == 4 ? reinterpret_cast<const void*>(&k_batch_push_c<Real, 4, false>)
+                        : reinterpret_cast<const void*>(&k_batch_push_c<Real, 1, false>);
+      }
       if (stage) return dep == 4 ? batch_push_shape<4, true>(shape) : batch_push_shape<1, true>(shape);
       return dep == 4 ? batch_push_shape<4, false>(shape) : batch_push_shape<1, false>(shape);
     }
@@ -1708,8 +1798,15 @@ struct Launchers {
       case 1: return BatchShape<1>::threads;
       case 2: return BatchShape<2>::threads;
       case 3: return BatchShape<3>::threads;
+      case 4: return 1024;
       default: return BatchShape<0>::threads;
     }
+  }
+
+  static cudaError_t batch_member_set(int index, const BatchMember* m, cudaStream_t st) {
+    if (index < 0 || index >= kConstMembers) return cudaErrorInvalidValue;
+    return cudaMemcpyToSymbolAsync(c_members, m, sizeof(BatchMember), sizeof(BatchMember) * (size_t)index,
+                                   cudaMemcpyHostToDevice, st);
   }
 
   // Launch configuration of the batched particle kernel for one variant:
@@ -1725,8 +1822,9 @@ struct Launchers {
     if (smem_bytes(max_nx, kSmemESmemS, dp) > limit && dp == 4) dp = 1;
     const size_t sm = smem_bytes(max_nx, kSmemESmemS, dp);
     if (sm > limit) return cudaErrorInvalidValue;
-    if (shape < 0 || shape > 3) return cudaErrorInvalidValue;
+    if (shape < 0 || shape > 4) return cudaErrorInvalidValue;
     if (stage && sizeof(Real) != 4) return cudaErrorInvalidValue;
+    if (!batch_push_fn(dp, shape, stage != 0)) return cudaErrorInvalidValue;
     const int threads = batch_threads(shape);
     if (stage) {
       int dev = 0, optin = 0, per_sm_max = 0;
@@ -1752,7 +1850,7 @@ struct Launchers {
     *block = threads;
     *smem = smem_total;
     // kernel selector: accumulator form, launch shape, staging
-    *dep = dp + 16 * shape + 64 * (stage ? 1 : 0);
+    *dep = dp + 16 * shape + 256 * (stage ? 1 : 0);
     return cudaSuccess;
   }
 
@@ -1765,8 +1863,10 @@ struct Launchers {
     if (before) cudaEventRecord(before, st);
     BatchDev arg = b;
     void* args[] = {&arg};
-    cudaError_t e = cudaLaunchKernel(batch_push_fn(dep % 16, (dep / 16) % 4, dep / 64 != 0), dim3(grid), dim3(block),
-                                     args, smem, st);
+    const int shape = (dep / 16) % 16;
+    // the constant-bank kernel: one row of max_ctas CTAs per member slot
+    const dim3 g = shape == 4 ? dim3(b.max_ctas, b.n) : dim3(grid);
+    cudaError_t e = cudaLaunchKernel(batch_push_fn(dep % 16, shape, dep / 256 != 0), g, dim3(block), args, smem, st);
     if (e != cudaSuccess) return e;
     if (after) cudaEventRecord(after, st);
     k_batch_field<Real><<<b.n, kFieldBlock, 0, st>>>(b);
@@ -1834,6 +1934,9 @@ struct Launchers {
     return Launchers<REAL>::batch_step(b, grid, block, smem, dep, s, before, after);              \
   }                                                                                               \
   size_t partial_bytes_##SUFFIX() { return sizeof(REAL); }                                       \
+  cudaError_t batch_member_set_##SUFFIX(int index, const BatchMember* m, cudaStream_t s) {          \
+    return Launchers<REAL>::batch_member_set(index, m, s);                                        \
+  }                                                                                               \
   cudaError_t histogram_##SUFFIX(const Dev& d, int sp, int q, int nb, double lo, double hi,          \
                                  unsigned long long* out, cudaStream_t s) {                       \
     return Launchers<REAL>::histogram(d, sp, q, nb, lo, hi, out, s);                              \

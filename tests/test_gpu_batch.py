@@ -226,7 +226,7 @@ def test_autotuned_scan_matches_oracle_and_caches_its_choice(tmp_path, monkeypat
     """Autotuning of the batched particle kernel (the scan's launch shape is
     picked by measurement).  The 256-cascade scan, armed to measure even on a
     cache hit, runs its first steps cycling through every candidate variant
-    (four launch shapes, with and without cp.async staging), one step each,
+    (five launch shapes, with and without cp.async staging), one step each,
     then continues with the fastest.  Every step was computed by whichever
     variant it drew, so the members' agreement with the FP64 oracle at step
     60 covers all candidates.  The choice is stored under the batch's size
@@ -279,3 +279,95 @@ def test_forced_variant_and_tuning_off(monkeypatch):
     with CascadeBatch([p]) as b:
         b.step([32])
         assert b.variant()["source"] == "forced" and b.variant()["shape"] == 2
+
+
+@pytest.mark.parametrize("precision,stage", [("fp32", 1), ("fp32", 0), ("fp32_fine", 1)])
+def test_constant_bank_kernel_matches_oracle(precision, stage):
+    """Launch shape 4, the constant-bank form of the batched particle kernel
+    (one row of CTAs per member, the member's descriptor read from the
+    constant bank by blockIdx.y): the uneven members of the FP64 test in
+    FP32, 80 steps through the first emissions and conversions, against the
+    FP64 oracle with the tolerances of the persistent kernel's test."""
+    ps = [dict(p, precision=precision) for p in members_fp64()]
+    steps = 80
+    with CascadeBatch(ps) as b:
+        b.set_variant(shape=4, stage=stage, prefetch=0 if stage else 1)
+        b.step([steps] * len(ps))
+        assert b.variant()["shape"] == 4
+        for i, p in enumerate(ps):
+            d = b.diag(i, steps)
+            E, _ = b.fields(i)
+            ref = oracle.Oracle(T.oracle_params(p))
+            d_ref = ref.step(steps)
+            E_ref, _ = ref.fields()
+            scale = np.abs(d_ref["E_absmax"]).max()
+            assert np.abs(E - E_ref).max() <= 5e-4 * scale, i
+            assert np.abs(d["E_mean"] - d_ref["E_mean"]).max() <= 5e-4 * scale, i
+            assert abs(d["n_pairs_total"][-1] - d_ref["n_pairs_total"][-1]) <= 0.02 * max(d_ref["n_pairs_total"][-1], 1)
+
+
+def test_constant_bank_kernel_on_the_scan_and_mid_run_admission():
+    """The constant-bank kernel on all 256 cascades of the scan (first 60
+    steps, five members against the oracle), then on a served batch where a
+    request joins two running members: the joining member's table entry is
+    written behind the queued steps, and its result matches the same request
+    run with the persistent kernel (first 100 steps to 1e-3 of max |E|)."""
+    scan = [dict(q) for q in W.batch_scan(256)]
+    for q in scan:
+        q.pop("steps")
+    steps = 60
+    order = sorted(range(len(scan)), key=lambda i: scan[i]["nx"] * scan[i]["ppc"])
+    picks = order[:2] + [order[len(order) // 2], order[-2], order[-1]]
+    with CascadeBatch(scan) as b:
+        b.set_variant(shape=4, stage=1, prefetch=0)
+        b.step([steps] * len(scan))
+        for i in picks:
+            p = scan[i]
+            E, _ = b.fields(i)
+            d = b.diag(i, steps)
+            ref = oracle.Oracle(T.oracle_params(p))
+            d_ref = ref.step(steps)
+            E_ref, _ = ref.fields()
+            assert np.abs(E - E_ref).max() <= 2e-4 * np.abs(E_ref).max(), i
+            for k in ("n_elec", "n_posi", "n_pairs_total"):
+                assert abs(d[k][-1] - d_ref[k][-1]) <= 0.01 * max(d_ref[k][-1], 1), (i, k)
+    req = W.small_cascade(precision="fp32")
+    others = [dict(q, precision="fp32") for q in members_fp64()[1:]]
+    out = {}
+    for shape, stage in ((4, 1), (3, 1)):
+        with CascadeBatch(slots=4, precision="fp32", max_nx=2048) as b:
+            b.set_variant(shape=shape, stage=stage, prefetch=0)
+            b.admit(others[0], 400)
+            b.admit(others[2], 400)
+            b.run(50)
+            slot = b.admit(req, 100)
+            got = []
+            for _ in range(200):
+                b.run(16)
+                got += b.poll()
+                if slot in got:
+                    break
+            assert slot in got
+            out[shape] = b.diag(slot, 100)
+    scale = np.abs(out[3]["E_absmax"]).max()
+    assert np.abs(out[4]["E_mean"] - out[3]["E_mean"]).max() <= 1e-3 * scale
+    assert abs(out[4]["n_pairs_total"][-1] - out[3]["n_pairs_total"][-1]) <= 0.01 * out[3]["n_pairs_total"][-1]
+
+
+def test_member_table_exhaustion_falls_back():
+    """The constant bank holds a few hundred member entries per precision: a
+    batch that finds no free slice keeps the shared-memory kernel (launch
+    shape 4 is refused for it), and the slice returns when its owner goes."""
+    a = CascadeBatch(slots=300, precision="fp32", max_nx=1024)
+    try:
+        a.set_variant(shape=4, stage=1, prefetch=0)
+        b = CascadeBatch(slots=300, precision="fp32", max_nx=1024)
+        try:
+            with pytest.raises(CascadeError):
+                b.set_variant(shape=4, stage=1, prefetch=0)
+        finally:
+            b.close()
+    finally:
+        a.close()
+    with CascadeBatch(slots=300, precision="fp32", max_nx=1024) as c:
+        c.set_variant(shape=4, stage=1, prefetch=0)
