@@ -146,6 +146,7 @@ def ensemble(rec: dict, params: dict | None = None) -> dict:
     zz = z[:9]
     omega = float(np.pi / np.mean(np.diff(zz))) if len(zz) > 2 else float("nan")
     lam, _ = damping_rate(t, E)
+    tp, vp = field_peaks(t, E)
     out = {
         "growth_rate": G,
         "screening_time": float(z[0]) if len(z) else float("nan"),
@@ -153,6 +154,9 @@ def ensemble(rec: dict, params: dict | None = None) -> dict:
         "oscillation_frequency": omega,
         "damping_rate": lam,
         "damping_eps0": float(4.0 * np.pi * lam / omega) if np.isfinite(lam) and omega > 0 else float("nan"),
+        # the envelope fell through the whole fit window (to 0.4 of its first
+        # peak): the damping rate is resolved, not a slope of noise
+        "damping_resolved": float(len(vp) > 2 and bool((vp < 0.4 * vp[0]).any())),
         "final_pairs": float(rec["n_pairs_total"][-1]) if len(t) else float("nan"),
         "final_energy": float((rec["U_E"] + rec["U_K"] + rec["U_gamma"])[-1]) if len(t) else float("nan"),
     }

@@ -69,7 +69,8 @@ def sweep_dt(E0: float, eps_gamma: float) -> float:
 def precision_sweep(run: int = 0, precision: str = "fp32") -> list:
     """Nx = 4096, 32 per species per cell, E0 in {10, 100, 1000}, gamma_thr in
     {20, 200, 2000}, eps = gamma_thr / 2, l_pp = 1, 5000 steps, dt from sweep_dt,
-    dx = 2 dt."""
+    dx = 2 dt; every step's record is kept (diag_ring > steps), since the
+    cascade and screening happen in the first steps."""
     out = []
     for E0 in (10.0, 100.0, 1000.0):
         for g in (20.0, 200.0, 2000.0):
@@ -77,7 +78,7 @@ def precision_sweep(run: int = 0, precision: str = "fp32") -> list:
             dt = sweep_dt(E0, eps)
             out.append(dict(nx=4096, ppc=32, dx=2 * dt, dt=dt, n0=1.0, u_spread=0.01, seed=seed_of(3, run),
                             E0=E0, gamma_thr=g, eps_gamma=eps, l_pp=1.0, particle_cap=250_000_000,
-                            precision=precision, steps=5000))
+                            precision=precision, steps=5000, diag_ring=8192))
     return out
 
 
