@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cap", type=int, default=0, help="particle cap per species (0 = the workload's)")
     ap.add_argument("--ppc", type=int, default=0, help="seed particles per cell per species (0 = the workload's)")
+    ap.add_argument("--u-words", type=int, default=0,
+                    help="FP32 momentum words (0 = chosen at creation, 2 = compensated pair: 28 B per particle-step)")
     ap.add_argument("--workload", default="large",
                     choices=["large", "batch", "serve", "sweep", "paper", "corotating", "damping", "parity"],
                     help="large: one large cascade (default); batch: the 256-cascade parameter scan in one "
@@ -318,6 +320,8 @@ def main():
         p["particle_cap"] = args.cap
     if args.ppc:
         p["ppc"] = args.ppc
+    if args.u_words:
+        p["u_words"] = args.u_words
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -327,6 +331,8 @@ def main():
 
     peak, peak_kind = measured_peak()
     bpp = BYTES_PER_PARTICLE_STEP[prec]
+    if prec == "fp32" and capi.cascade_momentum_words(p) == 2:
+        bpp += 4  # the low word of a two-word momentum, read and written
     c = Cascade(p)
     # the cascade phase, with emission and pair creation at every step
     casc = None
@@ -364,7 +370,7 @@ def main():
 
     avg_push_s = tim["particle_kernel_ms"] / 1e3 / max(tim["particle_kernel_launches"], 1)
     achieved = bpp * ps / args.steps / avg_push_s / 1e9
-    tb = MEASURED_DRAM_BYTES_PER_PARTICLE_STEP.get(prec)
+    tb = MEASURED_DRAM_BYTES_PER_PARTICLE_STEP.get(prec) if bpp == BYTES_PER_PARTICLE_STEP[prec] else None
     traffic = tb * ps / args.steps if tb else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_source": "ncu capture of a smaller case scaled per particle-step"

@@ -54,6 +54,82 @@ def stratified(params: list, n: int, key) -> list:
     return [params[order[int((k + 0.5) * len(params) / n)]] for k in range(n)]
 
 
+def shard_by_work(costs: list, world: int) -> list:
+    """Independent cascades over ``world`` GPUs by predicted work: the
+    largest first, each to the rank with the least work so far (ties to the
+    lower rank), so every rank computes the same assignment without any
+    exchange.  Returns each rank's member indices in their original order."""
+    if world < 1:
+        raise ValueError("world must be at least 1")
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda i: (-float(costs[i]), i)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        out[r].append(i)
+        load[r] += float(costs[i])
+    return [sorted(x) for x in out]
+
+
+def route_requests(costs: list, world: int) -> list:
+    """Requests in arrival order to ``world`` GPUs: each to the rank whose
+    requests so far add up to the least predicted work (ties to the lower
+    rank).  Deterministic, so every rank routes the same trace alike.
+    Returns the rank of each request."""
+    if world < 1:
+        raise ValueError("world must be at least 1")
+    load = [0.0] * world
+    out = []
+    for c in costs:
+        r = min(range(world), key=lambda r: (load[r], r))
+        out.append(r)
+        load[r] += float(c)
+    return out
+
+
+def merge_served(parts: list) -> dict:
+    """Whole-job serving figures from the ranks' own: the particle-steps of
+    all ranks over the slowest rank's wall time, and percentiles over every
+    request's times (each part holds its requests' times to result and waits
+    for admission)."""
+    ps = sum(x["particle_steps"] for x in parts)
+    wall = max(x["wall_s"] for x in parts)
+    ttr = np.concatenate([np.asarray(x["ttr"], float) for x in parts])
+    wait = np.concatenate([np.asarray(x["wait"], float) for x in parts])
+    n = int(sum(x["requests"] for x in parts))
+    return {"particle_steps": ps, "wall_s": wall, "value": ps / wall if wall > 0 else None, "requests": n,
+            "p50_time_to_result_s": float(np.percentile(ttr, 50)) if len(ttr) else None,
+            "p99_time_to_result_s": float(np.percentile(ttr, 99)) if len(ttr) else None,
+            "p50_wait_for_admission_s": float(np.percentile(wait, 50)) if len(wait) else None,
+            "p99_wait_for_admission_s": float(np.percentile(wait, 99)) if len(wait) else None,
+            "busy_rejections": int(sum(x["busy_rejections"] for x in parts)),
+            "requests_per_s": n / wall if wall > 0 else None, "ranks": len(parts)}
+
+
+def _ranks():
+    """(rank, world) of a torchrun launch, with this rank's GPU selected and
+    the process group up when there are several; (0, 1) otherwise."""
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world
+
+
+def _gather(obj, world: int) -> list:
+    import torch.distributed as dist
+
+    if world == 1:
+        return [obj]
+    out = [None] * world
+    dist.all_gather_object(out, obj)
+    return out
+
+
 def _sample_note(n_sample: int, n_all: int, what: str) -> str:
     if n_sample >= n_all:
         return f"all {n_all} {what}, each alone in FP64"
@@ -67,10 +143,19 @@ def run_batch(args) -> int:
     from paper_2012_05587_gb300 import CascadeBatch, capi, workloads as W
 
     prec = args.precision
-    scan = W.batch_scan(args.batch_n, precision=prec, steps=args.batch_steps)
+    rank, world = _ranks()
+    full = W.batch_scan(args.batch_n, precision=prec, steps=args.batch_steps)
+    # several GPUs: each runs its share of the scan, balanced by predicted work
+    mine = shard_by_work([W.predicted_particles(p) for p in full], world)[rank]
+    scan = [full[i] for i in mine]
     footprint = sum(capi.cascade_footprint(p)[1] for p in scan)
     predicted = sum(W.predicted_particles(p) for p in scan)
     stream = torch.cuda.current_stream()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        torch.cuda.synchronize()
     t0 = time.perf_counter()
     b = CascadeBatch(scan)
     torch.cuda.synchronize()
@@ -101,17 +186,29 @@ def run_batch(args) -> int:
         pairs += int(d["n_pairs_total"][-1])
         photons += int(d["n_pairs_total"][-1] + d["n_photon"][-1])
     b.close()
-    value = ps / (ms / 1e3)
     roof = _batch_roofline(scan, args.batch_steps, prec)
-    sample = stratified(scan, args.fp64_sample, lambda p: W.predicted_particles(p))
+    ms, ps = B.aggregate_over_ranks(ms, ps)
+    pairs = int(sum(_gather(pairs, world)))
+    photons = int(sum(_gather(photons, world)))
+    over = int(sum(_gather(over, world)))
+    value = ps / (ms / 1e3)
+    if rank != 0:
+        return 0
+    if world > 1:
+        footprint = sum(capi.cascade_footprint(p)[1] for p in full)
+        predicted = sum(W.predicted_particles(p) for p in full)
+    sample = stratified(full, args.fp64_sample, lambda p: W.predicted_particles(p))
     fp64 = _fp64_one_at_a_time(sample, lambda p: args.batch_steps)
     line = {
-        "metric": B.METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.batch_steps, "warmup": 0,
-        "ms_per_step": ms / args.batch_steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": B.METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.batch_steps,
+        "warmup": 0, "ms_per_step": ms / args.batch_steps, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
         "dtype": "f32" if prec.startswith("fp32") else "f64", "data": "synthetic",
-        "config": {"workload": f"batched parameter scan: {len(scan)} cascades (Nx log-U[256,8192], ppc in "
+        "config": {"workload": f"batched parameter scan: {len(full)} cascades (Nx log-U[256,8192], ppc in "
                                "{8,16,32,64}, E0 and gamma_thr log-U[10,1000], eps = gamma_thr/2, l_pp U[0.2,2]), "
                                f"{args.batch_steps} steps each, {prec}, one launch per kernel per step",
+                   "parallelism": (f"{world} GPUs, the scan's cascades shared by predicted work, one batch "
+                                   "per GPU, no data-path exchange") if world > 1 else "single GPU",
                    "members_over_capacity": over, "create_s": t_create, "wall_s": wall,
                    "device_footprint_bytes": footprint, "predicted_particles_at_screening": predicted,
                    "pairs_created_per_particle_step": pairs / ps if ps else None,
@@ -147,7 +244,7 @@ def batch_scan_summary(steps: int = 300, n: int = 256, prec: str = "fp32") -> di
     # the default launch variant, no tuning pass: 300 steps are the growth
     # phase of most members, which would tune for the wrong state and store
     # that choice under the full scan's size class (on the full scan the
-    # tuner keeps the default variant)
+    # tuner picks the default variant, the constant-bank kernel, staged)
     b.tune_next(rounds=0)
     capi.cascade_batch_set_timing(b.b, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -190,6 +287,8 @@ def serve_summary(requests: int = 150, rate: float = 5.0, prec: str = "fp32") ->
         out = _serve(reqs, prec, budget)
     finally:
         torch.cuda.set_stream(prev)
+    out.pop("ttr", None)
+    out.pop("wait", None)
     out["workload"] = (f"serving: {requests} requests of the serving distribution, Poisson arrivals at {rate}/s, "
                        "admission by predicted device footprint, continuous batching")
     out["unit"] = UNIT
@@ -291,7 +390,8 @@ def _serve(reqs: list, prec: str, budget: int) -> dict:
             "p99_time_to_result_s": float(np.percentile(ttr, 99)),
             "p50_wait_for_admission_s": float(np.percentile(wait, 50)),
             "p99_wait_for_admission_s": float(np.percentile(wait, 99)),
-            "busy_rejections": busy_rejects, "requests_per_s": len(reqs) / wall}
+            "busy_rejections": busy_rejects, "requests_per_s": len(reqs) / wall,
+            "ttr": ttr.tolist(), "wait": wait.tolist()}
 
 
 def run_serve(args) -> int:
@@ -300,7 +400,12 @@ def run_serve(args) -> int:
     from paper_2012_05587_gb300 import workloads as W
 
     prec = args.precision
-    reqs = W.serving_requests(args.requests, rate=args.rate, precision=prec)
+    rank, world = _ranks()
+    reqs_all = W.serving_requests(args.requests, rate=args.rate, precision=prec)
+    # several GPUs: one server per GPU, each request routed on arrival to the
+    # GPU with the least predicted work routed to it so far
+    route = route_requests([W.predicted_particles(r) * r["steps"] for r in reqs_all], world)
+    reqs = [r for r, k in zip(reqs_all, route) if k == rank]
     free = torch.cuda.mem_get_info()[0]
     budget = int(0.6 * free)
     # a private stream: host reads of finished requests never wait for the batch
@@ -308,7 +413,11 @@ def run_serve(args) -> int:
     torch.cuda.set_stream(serve_stream)
     sampler = B.ClockSampler(torch.cuda.current_device())
     sampler.start()
-    sat = _serve(reqs, prec, budget)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    sat = merge_served(_gather(_serve(reqs, prec, budget), world))
     clocks = sampler.stop()
     # the same request distribution at a fraction of the capacity just
     # measured (requests completed per second while saturated), so that the
@@ -316,25 +425,35 @@ def run_serve(args) -> int:
     low = None
     if args.serve_low_frac > 0 and args.serve_low_requests > 0:
         rate = args.serve_low_frac * sat["requests_per_s"]
-        reqs_low = W.serving_requests(args.serve_low_requests, rate=rate, run=1, precision=prec)
-        low = _serve(reqs_low, prec, budget)
+        low_all = W.serving_requests(args.serve_low_requests, rate=rate, run=1, precision=prec)
+        route_low = route_requests([W.predicted_particles(r) * r["steps"] for r in low_all], world)
+        reqs_low = [r for r, k in zip(low_all, route_low) if k == rank]
+        low = merge_served(_gather(_serve(reqs_low, prec, budget), world))
         low["arrival_rate_per_s"] = rate
-        low["what"] = (f"{len(reqs_low)} requests of the same distribution (another seed) arriving at "
+        low.pop("ttr", None)
+        low.pop("wait", None)
+        low["what"] = (f"{len(low_all)} requests of the same distribution (another seed) arriving at "
                        f"{args.serve_low_frac} of the capacity measured by the saturated run")
+    if rank != 0:
+        return 0
     n_fp64 = args.fp64_sample if args.fp64_sample > 0 else 64
-    sample = stratified(reqs, n_fp64, lambda p: W.predicted_particles(p) * p["steps"])
+    sample = stratified(reqs_all, n_fp64, lambda p: W.predicted_particles(p) * p["steps"])
     fp64 = _fp64_one_at_a_time(sample, lambda p: p["steps"])
+    reqs = reqs_all
     line = {
-        "metric": B.METRIC, "value": sat["value"], "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 0,
-        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": B.METRIC, "value": sat["value"], "unit": UNIT, "n_gpus": world, "steps": len(reqs), "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None,
         "dtype": "f32" if prec.startswith("fp32") else "f64", "data": "synthetic",
         "config": {"workload": f"serving: {len(reqs)} requests, Poisson arrivals {args.rate}/s, parameters from "
                                "the batch scan, steps U[500,5000], admission by predicted device footprint "
                                f"(budget {budget / 1e9:.1f} GB), continuous batching",
+                   "parallelism": (f"{world} GPUs, one server each, requests routed by predicted work"
+                                   if world > 1 else "single GPU"),
                    "busy_rejections": sat["busy_rejections"], "wall_s": sat["wall_s"]},
         "p50_time_to_result_s": sat["p50_time_to_result_s"],
         "p99_time_to_result_s": sat["p99_time_to_result_s"],
-        "saturated": sat,
+        "saturated": {k: v for k, v in sat.items() if k not in ("ttr", "wait")},
         "below_capacity": low,
         "fp64_alone": dict(fp64, p50_s=float(np.percentile(fp64["per_request_s"], 50)),
                            p99_s=float(np.percentile(fp64["per_request_s"], 99)), per_request_s=None,
@@ -395,6 +514,11 @@ def run_sweep(args) -> int:
             row["fp64_mean"] = mean["fp64"]
             row["fp32_rel_err"] = analysis.relative_errors(mean["fp32"], mean["fp64"])
             row["fp32_fine_rel_err"] = analysis.relative_errors(mean["fp32_fine"], mean["fp64"])
+            # seed by seed: the signed relative difference of the means and its
+            # standard error, which tells a bias from the chaotic spread
+            for k in ("fp32", "fp32_fine"):
+                pc = analysis.paired_comparison(res[k], res["fp64"])
+                row[k + "_paired"] = {f: [v["rel_err"], v["rel_se"]] for f, v in pc.items()}
         row["seconds"] = time.perf_counter() - t_row
         rows.append(row)
         print(json.dumps({"sweep_row": row}), flush=True)
