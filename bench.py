@@ -532,9 +532,11 @@ def e2e_run(c, p, steps, stream, barrier):
     # ~6 GB state adds about 60 ms of cudaMalloc to the upload)
     c.close()
     barrier()
+    reserved0 = torch.cuda.memory_reserved()
     t0 = time.perf_counter()
     c2 = Cascade(p, state={"elec": host[0], "posi": host[1], "E": hE})
     t_up = time.perf_counter() - t0
+    grew = torch.cuda.memory_reserved() - reserved0
     ps = 0.0
     for _ in range(steps):
         c2.step(1)
@@ -552,11 +554,21 @@ def e2e_run(c, p, steps, stream, barrier):
     barrier()
     t_again = time.perf_counter() - t1
     c3.close()
+    # outside the metric: the same host arrays copied by torch alone, which
+    # tells the host memory's copy rate from the library's own upload costs
+    barrier()
+    t2 = time.perf_counter()
+    raw = [torch.from_numpy(host[s][k]).to(stream.device, non_blocking=True) for s in (0, 1)
+           for k in ("cell", "off", "u")]
+    barrier()
+    t_raw = time.perf_counter() - t2
+    del raw
     h2d = sum(host[s][k].nbytes for s in (0, 1) for k in ("cell", "off", "u")) + hE.nbytes
     d2h = 112 * steps + E2.nbytes + J2.nbytes
     return {"value": ps / el, "unit": UNIT, "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
             "seconds": el, "create_and_upload_s": t_up, "steps_and_reads_s": el - t_up,
-            "create_and_upload_again_s": t_again,
+            "create_and_upload_again_s": t_again, "plain_copy_of_the_host_arrays_s": t_raw,
+            "device_memory_reserved_by_the_first_upload_bytes": grew,
             "what": "cascade_create_from_state(_f32) from pinned host arrays (int32 cell, offset and momentum in "
                     "the cascade's precision) + per step cascade_step(1) and cascade_diag(1) to host + final E/J "
                     "to host; wall clock"}

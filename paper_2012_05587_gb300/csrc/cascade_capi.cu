@@ -1158,7 +1158,14 @@ int batch_tune_with_warmup(cascade_batch_t* b, long long* steps, long long warmu
 
 // Batch members keep one-word FP32 momenta (the batched particle kernel has
 // no two-word form).
-int batch_member_words(const cascade_params* p) {
+// What a batch member may not be: two-word FP32 momenta, or more particles
+// per species than the batched kernel's 32-bit chunk indices cover.
+int batch_member_params(const cascade_params* p) {
+  if (p->particle_cap > kBatchMaxCap) {
+    snprintf(g_msg, sizeof(g_msg), "batch members hold at most %lld particles per species (particle_cap %lld)",
+             (long long)kBatchMaxCap, (long long)p->particle_cap);
+    return CASCADE_ERR_INVALID_ARG;
+  }
   int words = 1;
   int rc = momentum_words(p, &words);
   if (rc) return rc;
@@ -1329,7 +1336,7 @@ int cascade_batch_admit(cascade_batch_t* b, const cascade_params* params, int32_
     snprintf(g_msg, sizeof(g_msg), "batch members are periodic (open_bc = 0)");
     return CASCADE_ERR_INVALID_ARG;
   }
-  if ((rc = batch_member_words(params))) return rc;
+  if ((rc = batch_member_params(params))) return rc;
   if (params->nx > b->max_nx) {
     snprintf(g_msg, sizeof(g_msg), "member nx = %d exceeds the batch's max_nx = %d", params->nx, b->max_nx);
     return CASCADE_ERR_INVALID_ARG;
@@ -1403,7 +1410,7 @@ int cascade_batch_create(const cascade_params* params, int32_t n, size_t hbm_bud
       snprintf(g_msg, sizeof(g_msg), "member %d: batch members are periodic (open_bc = 0)", i);
       return CASCADE_ERR_INVALID_ARG;
     }
-    if (batch_member_words(&params[i])) {
+    if (batch_member_params(&params[i])) {
       char why[sizeof(g_msg)];
       snprintf(why, sizeof(why), "%s", g_msg);
       snprintf(g_msg, sizeof(g_msg), "member %d: %s", i, why);

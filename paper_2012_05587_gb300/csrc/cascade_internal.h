@@ -108,6 +108,9 @@ struct BatchMember {
 };
 
 // Entries of the constant-bank member table in each kernel translation unit.
+// particles per species a batch member may hold: the batched kernel indexes
+// 4-particle chunks and particles of one member with 32-bit integers
+constexpr long long kBatchMaxCap = 1LL << 30;
 constexpr int kConstMembers = 64 * 1024 / sizeof(BatchMember) - 8;
 
 // A batch of cascades advanced together (one launch per kernel per step).

@@ -1259,18 +1259,22 @@ __device__ __forceinline__ void batch_member_range(const BatchDev& b, const DevT
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double gsum = 0.0;
-  const long long iters = (e - a + blockDim.x - 1) / blockDim.x;
+  // chunk and particle indices in 32 bits: a batch member holds at most
+  // 2^30 particles per species (checked at admission)
+  const int a32 = (int)a, e32 = (int)e, c0 = (int)C0, n0 = (int)N0, n1 = (int)N1;
+  const int nthr = (int)blockDim.x, tid = (int)threadIdx.x;
+  const int iters = (e32 - a32 + nthr - 1) / nthr;
   const int pf = b.prefetch;
   // this thread's staging slots (STG): [stage][array][thread][16 B]
   const size_t slab = (size_t)blockDim.x * 16;
   auto slot_of = [&](int bb, int arr) { return stage + (size_t)(bb * 3 + arr) * slab + (size_t)threadIdx.x * 16; };
-  auto issue = [&](long long it) {  // cp.async of iteration it's chunk into stage it & 1
-    const long long ch = a + it * blockDim.x + warp * 32 + lane;
-    if (it < iters && ch < e) {
-      const int sp = ch < C0 ? 0 : 1;
-      const long long bp = (ch - (sp ? C0 : 0)) * 4;
-      const unsigned bytes = (unsigned)min(4LL, (sp ? N1 : N0) - bp) * 4u;
-      const int bb = (int)(it & 1);
+  auto issue = [&](int it) {  // cp.async of iteration it's chunk into stage it & 1
+    const int ch = a32 + it * nthr + tid;
+    if (it < iters && ch < e32) {
+      const int sp = ch < c0 ? 0 : 1;
+      const int bp = (ch - (sp ? c0 : 0)) * 4;
+      const unsigned bytes = (unsigned)min(4, (sp ? n1 : n0) - bp) * 4u;
+      const int bb = it & 1;
       cp_async16(slot_of(bb, 0), d.cell[sp] + bp, bytes);
       cp_async16(slot_of(bb, 1), static_cast<const Real*>(d.off[sp]) + bp, bytes);
       cp_async16(slot_of(bb, 2), static_cast<const Real*>(d.u[sp]) + bp, bytes);
@@ -1278,13 +1282,13 @@ __device__ __forceinline__ void batch_member_range(const BatchDev& b, const DevT
     cp_async_commit();  // one group per iteration, empty or not
   };
   if (STG) issue(0);
-  for (long long it = 0; it < iters; ++it) {
+  for (int it = 0; it < iters; ++it) {
     if (pf > 0 && lane == 0) {
       // the warp's particles pf iterations ahead, inside this range
-      const long long chp = a + (it + pf) * blockDim.x + warp * 32;
-      if (chp < e) {
-        const int sp = chp < C0 ? 0 : 1;
-        const long long bp = (chp - (sp ? C0 : 0)) * 4;
+      const int chp = a32 + (it + pf) * nthr + warp * 32;
+      if (chp < e32) {
+        const int sp = chp < c0 ? 0 : 1;
+        const long long bp = (long long)(chp - (sp ? c0 : 0)) * 4;
         long long np = d.cap4 - bp;  // stay inside the allocation
         if (np > 128) np = 128;
         if (np > 0) {
@@ -1294,18 +1298,17 @@ __device__ __forceinline__ void batch_member_range(const BatchDev& b, const DevT
         }
       }
     }
-    const long long ch = a + it * blockDim.x + warp * 32 + lane;
-    int s = 0, cnt = 0;
-    long long base = 0;
-    if (ch < e) {
-      s = ch < C0 ? 0 : 1;
-      base = (ch - (s ? C0 : 0)) * 4;
-      cnt = (int)min(4LL, (s ? N1 : N0) - base);
+    const int ch = a32 + it * nthr + tid;
+    int s = 0, cnt = 0, base = 0;
+    if (ch < e32) {
+      s = ch < c0 ? 0 : 1;
+      base = (ch - (s ? c0 : 0)) * 4;
+      cnt = min(4, (s ? n1 : n0) - base);
     }
     if (STG) {
       issue(it + 1);
       cp_async_wait_prev();  // iteration it's copies have landed
-      const int bb = (int)(it & 1);
+      const int bb = it & 1;
       const unsigned char* stg[3] = {slot_of(bb, 0), slot_of(bb, 1), slot_of(bb, 2)};
       gsum += (double)process4<Real, kSmemESmemS, DEP, true, false, true, false, DevT>(d, st, s, base, cnt, lane,
                                                                                     stg);

@@ -90,10 +90,12 @@ def test_create_without_device_fails_cleanly():
     ([dict(eps_gamma=1.5)], "member 0: invalid parameters: eps_gamma"),
     ([{}, dict(precision="fp64")], "member 1: precision"),
     ([{}, {}, dict(open_bc=1)], "member 2: batch members are periodic"),
+    ([{}, dict(particle_cap=(1 << 30) + 1)], "member 1: batch members hold at most 1073741824 particles"),
 ])
 def test_batch_members_validated_before_device_work(members, why):
     """A batch checks every member on the host (the same domain as a single
-    cascade, one precision class, periodic grids) before touching a device."""
+    cascade, one precision class, periodic grids, at most 2^30 particles per
+    species) before touching a device."""
     ps = [dict(W.small_cascade(precision="fp32"), **m) for m in members]
     with pytest.raises(capi.CascadeError) as ei:
         capi.cascade_batch_create(ps, 0, 0)
