@@ -10,7 +10,12 @@ one seed start from the same noise and stay close (their damping rates
 correlate at 0.98), but drift apart after the parity horizon, so the means
 of 16 seeds differ by sampling noise as well as by any bias.  Those two are
 required to agree to 2% up to three standard errors of the paired
-difference; the test prints the measured difference and its error."""
+difference; the test prints the measured difference and its error.  The
+FP32 runs are also compared with the FP64 oracle's values of the same 32
+seeds (tests/golden/damping_oracle.json), under the same bounds."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -49,6 +54,38 @@ def test_fp32_against_fp64(ensembles):
     cmp = A.paired_comparison(ensembles["fp32"], ensembles["fp64"], DETERMINISTIC + CHAOTIC)
     for k, v in cmp.items():
         print(f"{k:28s} fp32 {v['mean']:.6g} fp64 {v['ref_mean']:.6g} rel {v['rel_err']:+.4f} +- {v['rel_se']:.4f}")
+    for k in DETERMINISTIC:
+        assert abs(cmp[k]["rel_err"]) <= TOL, k
+    for k in CHAOTIC:
+        assert abs(cmp[k]["rel_err"]) <= TOL + 3 * cmp[k]["rel_se"], k
+
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "damping_oracle.json")
+
+
+def test_fp32_against_the_oracle(ensembles):
+    """The same cascade against the FP64 oracle, seed by seed: the oracle's
+    ensemble diagnostics of runs 0 .. 31 are stored in
+    tests/golden/damping_oracle.json (written by
+    tests/golden/make_damping_oracle.py, which runs the oracle only).  The
+    FP32 runs of the fixture cover the first 16 seeds; the rest run here.
+    The same bounds as against the GPU's FP64 mode: 2% on the diagnostics
+    the cascade fixes, 2% up to three standard errors of the seed-by-seed
+    differences on those the instability decides."""
+    with open(GOLD) as f:
+        refs = json.load(f)["runs"]
+    runs = list(ensembles["fp32"])
+    for run in range(len(runs), len(refs)):
+        p = W.damping_cascade(run=run, precision="fp32")
+        with Cascade(p) as c:
+            c.step(p["steps"])
+            runs.append(A.ensemble(c.diag(p["steps"]), p))
+    for run, ref in enumerate(refs):
+        assert ref["seed"] == W.damping_cascade(run=run, precision="fp32")["seed"]
+    cmp = A.paired_comparison(runs[:len(refs)], refs, DETERMINISTIC + CHAOTIC)
+    for k, v in cmp.items():
+        print(f"{k:28s} fp32 {v['mean']:.6g} oracle {v['ref_mean']:.6g} rel {v['rel_err']:+.4f} "
+              f"+- {v['rel_se']:.4f} ({v['n']} seeds)")
     for k in DETERMINISTIC:
         assert abs(cmp[k]["rel_err"]) <= TOL, k
     for k in CHAOTIC:
