@@ -502,7 +502,7 @@ def e2e_run(c, p, steps, stream, barrier):
     (cascade_diag), finally read E and J.  Closes c."""
     import torch
 
-    from paper_2012_05587_gb300 import Cascade
+    from paper_2012_05587_gb300 import Cascade, capi
 
     cnt = c.counts()
     ne, npo = cnt["n_elec"], cnt["n_posi"]
@@ -537,11 +537,20 @@ def e2e_run(c, p, steps, stream, barrier):
     c2 = Cascade(p, state={"elec": host[0], "posi": host[1], "E": hE})
     t_up = time.perf_counter() - t0
     grew = torch.cuda.memory_reserved() - reserved0
+    # every step's record reaches the host: queued behind its step, read
+    # while the next steps run, the last ones waited for at the end
     ps = 0.0
+    got = 0
     for _ in range(steps):
         c2.step(1)
-        r = c2.diag(1)
-        ps += float(r["n_elec"][-1] + r["n_posi"][-1])
+        c2.record_enqueue()
+        r = c2.record_poll()
+        ps += float((r["n_elec"] + r["n_posi"]).sum())
+        got += len(r["step"])
+    r = c2.record_poll(wait=True)
+    ps += float((r["n_elec"] + r["n_posi"]).sum())
+    got += len(r["step"])
+    assert got == steps, (got, steps)
     E2, J2 = c2.fields()
     barrier()
     el = time.perf_counter() - t0
@@ -564,14 +573,15 @@ def e2e_run(c, p, steps, stream, barrier):
     t_raw = time.perf_counter() - t2
     del raw
     h2d = sum(host[s][k].nbytes for s in (0, 1) for k in ("cell", "off", "u")) + hE.nbytes
-    d2h = 112 * steps + E2.nbytes + J2.nbytes
+    d2h = capi.cascade_record_copy_bytes() * steps + E2.nbytes + J2.nbytes
     return {"value": ps / el, "unit": UNIT, "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
             "seconds": el, "create_and_upload_s": t_up, "steps_and_reads_s": el - t_up,
             "create_and_upload_again_s": t_again, "plain_copy_of_the_host_arrays_s": t_raw,
             "device_memory_reserved_by_the_first_upload_bytes": grew,
             "what": "cascade_create_from_state(_f32) from pinned host arrays (int32 cell, offset and momentum in "
-                    "the cascade's precision) + per step cascade_step(1) and cascade_diag(1) to host + final E/J "
-                    "to host; wall clock"}
+                    "the cascade's precision) + per step cascade_step(1), cascade_record_enqueue and a "
+                    "non-blocking cascade_record_poll (every step's record read to the host, the last ones "
+                    "waited for) + final E/J to host; wall clock"}
 
 
 if __name__ == "__main__":

@@ -178,6 +178,22 @@ int cascade_sync(cascade_t* h);
 int cascade_diag(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t* n_out,
                  double* E_host, double* J_host);
 
+/* Per-step records without a wait (for a host loop that reads every step's
+ * result while the next step runs).  cascade_record_enqueue queues, behind
+ * the work queued on the cascade's stream so far, a copy of the newest
+ * step's record (the one cascade_diag returns last) into pinned host memory
+ * the library holds, and returns at once.  At most 64 copies may be queued
+ * and not yet polled; a further call returns CASCADE_ERR_BUSY and queues
+ * nothing.  cascade_record_poll hands back up to max queued records, oldest
+ * first, into host_out: with wait = 0 those that have landed (possibly none,
+ * *n_out = 0), with wait != 0 it waits for each one it returns.  Returns the
+ * cascade's sticky error status, like cascade_diag. */
+int cascade_record_enqueue(cascade_t* h);
+int cascade_record_poll(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t wait, int32_t* n_out);
+/* Bytes one queued copy moves to the host (the record with the step's
+ * counters and error flag; no device needed). */
+int32_t cascade_record_copy_bytes(void);
+
 /* Synchronise and compute Gauss's-law residual max_i |E_{i+1/2} - E_{i-1/2} -
  * dx rho_i| of the current state (rho from the CIC shape); it is also stored
  * in the newest per-step record. */

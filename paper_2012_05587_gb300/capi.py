@@ -105,6 +105,9 @@ def load() -> ctypes.CDLL:
             "cascade_step": ([vp, i32], ctypes.c_int),
             "cascade_sync": ([vp], ctypes.c_int),
             "cascade_diag": ([vp, vp, i32, P(i32), vp, vp], ctypes.c_int),
+            "cascade_record_enqueue": ([vp], ctypes.c_int),
+            "cascade_record_poll": ([vp, vp, i32, i32, P(i32)], ctypes.c_int),
+            "cascade_record_copy_bytes": ([], ctypes.c_int32),
             "cascade_gauss": ([vp, P(f64)], ctypes.c_int),
             "cascade_set_gauss_every": ([vp, i32], ctypes.c_int),
             "cascade_counts": ([vp, P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
@@ -268,6 +271,25 @@ def cascade_diag(h, max_records: int, nx: int | None = None, fields: bool = Fals
     a = np.frombuffer(buf, dtype=DIAG_DTYPE)[: n.value]
     rec = {f: a[f].copy() for f in DIAG_FIELDS}
     return (rec, E, J) if fields else rec
+
+
+def cascade_record_enqueue(h) -> None:
+    check("cascade_record_enqueue", load().cascade_record_enqueue(h))
+
+
+def cascade_record_copy_bytes() -> int:
+    return int(load().cascade_record_copy_bytes())
+
+
+def cascade_record_poll(h, max_records: int = 64, wait: bool = False) -> dict:
+    """Queued per-step records that have landed (all of them, waiting, with
+    ``wait``), oldest first, as numpy columns."""
+    buf = (cascade_diag_t * max(max_records, 1))()
+    n = ctypes.c_int32()
+    check("cascade_record_poll", load().cascade_record_poll(h, buf, int(max_records), int(bool(wait)),
+                                                            ctypes.byref(n)))
+    a = np.frombuffer(buf, dtype=DIAG_DTYPE)[: n.value]
+    return {f: a[f].copy() for f in DIAG_FIELDS}
 
 
 def cascade_gauss(h) -> float:

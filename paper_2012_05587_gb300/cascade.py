@@ -43,6 +43,14 @@ class Cascade:
     def diag(self, max_records: int = 1 << 16) -> dict:
         return capi.cascade_diag(self.h, max_records)
 
+    def record_enqueue(self) -> None:
+        """Queue a copy of the newest step's record to the host (no wait)."""
+        capi.cascade_record_enqueue(self.h)
+
+    def record_poll(self, max_records: int = 64, wait: bool = False) -> dict:
+        """The queued records that have landed, oldest first."""
+        return capi.cascade_record_poll(self.h, max_records, wait)
+
     def fields(self):
         _, E, J = capi.cascade_diag(self.h, 0, self.nx, fields=True)
         return E, J

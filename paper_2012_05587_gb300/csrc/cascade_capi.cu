@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
 #include <mutex>
 #include <new>
 #include <string>
@@ -107,6 +108,8 @@ int n_pp_of(const cascade_params* p) {
 
 }  // namespace
 
+constexpr int kRecRing = 64;  // record copies a cascade may have queued
+
 struct cascade {
   cascade_params p{};
   Dev d{};
@@ -129,6 +132,10 @@ struct cascade {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   long long kernels_launched = 0;
+  // queued copies of the newest record (cascade_record_enqueue / _poll)
+  Ctl* h_rec = nullptr;  // pinned, kRecRing copies of the control block
+  cudaEvent_t ev_rec[kRecRing] = {};
+  long long rec_issued = 0, rec_read = 0;
 
   void* dalloc(size_t n) {
     n = (n + 255) & ~size_t(255);
@@ -304,6 +311,27 @@ int setup(const cascade_params* params, void* stream, cascade_t** out, bool batc
   return CASCADE_OK;
 }
 
+// Phase timing of a state upload, for diagnosis: with CASCADE_TRACE_UPLOAD=1
+// each mark waits for the stream and prints the host time since the
+// previous mark to stderr.  Off by default (the waits serialise the upload).
+struct UploadTrace {
+  bool on = false;
+  std::chrono::steady_clock::time_point t0;
+  explicit UploadTrace() {
+    const char* v = getenv("CASCADE_TRACE_UPLOAD");
+    on = v && *v && atoi(v) != 0;
+    t0 = std::chrono::steady_clock::now();
+  }
+  void mark(cascade_t* h, const char* what) {
+    if (!on) return;
+    if (h) cudaStreamSynchronize(h->stream);
+    const auto t1 = std::chrono::steady_clock::now();
+    fprintf(stderr, "cascade upload: %-28s %8.2f ms\n", what,
+            std::chrono::duration<double, std::milli>(t1 - t0).count());
+    t0 = t1;
+  }
+};
+
 int upload_E(cascade_t* h, const double* E_host) {
   std::vector<double> E(h->d.nx, h->p.E0);
   if (E_host) memcpy(E.data(), E_host, sizeof(double) * h->d.nx);
@@ -328,6 +356,8 @@ int upload_species(cascade_t* h, int s, long long n, const int32_t* cell, const 
     stage = nullptr;
   }
   if (!stage) return CASCADE_ERR_OOM;
+  UploadTrace tr;
+  tr.mark(h, "  staging buffer");
   H* so = static_cast<H*>(stage);
   H* su = so + chunk;
   const int f32 = sizeof(H) == sizeof(float) ? 1 : 0;
@@ -344,10 +374,12 @@ int upload_species(cascade_t* h, int s, long long n, const int32_t* cell, const 
       e = h->real_size == sizeof(double) ? upload_fp64(h->d, s, k, m, so, su, f32, bad, h->stream)
                                          : upload_fp32(h->d, s, k, m, so, su, f32, bad, h->stream);
   }
+  tr.mark(h, "  copies and rounding");
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (h->free_fn) h->free_fn(stage, (void*)h->stream, h->alloc_ctx);
   else cudaFree(stage);
+  tr.mark(h, "  staging freed");
   if (e != cudaSuccess) return cuda_fail(e, "state upload");
   if (nbad) {
     snprintf(g_msg, sizeof(g_msg), "%u particles of species %d outside the grid or not finite", nbad, s);
@@ -458,15 +490,21 @@ int cascade_create_from_state(const cascade_params* params, int64_t n_elec, cons
   if ((n_elec > 0 && (!cell_e || !off_e || !u_e)) || (n_posi > 0 && (!cell_p || !off_p || !u_p)))
     return CASCADE_ERR_INVALID_ARG;
   cascade_t* h = nullptr;
+  UploadTrace tr;
   int rc = setup(params, cuda_stream, &h);
+  tr.mark(rc == CASCADE_OK ? h : nullptr, "setup (allocations)");
   if (rc == CASCADE_OK && (n_elec > params->particle_cap || n_posi > params->particle_cap)) {
     snprintf(g_msg, sizeof(g_msg), "state exceeds particle_cap");
     rc = CASCADE_ERR_CAPACITY;
   }
   if (rc == CASCADE_OK) rc = upload_E(h, E_host);
+  tr.mark(rc == CASCADE_OK ? h : nullptr, "E");
   if (rc == CASCADE_OK) rc = upload_species(h, 0, n_elec, cell_e, off_e, u_e);
+  tr.mark(rc == CASCADE_OK ? h : nullptr, "species 0");
   if (rc == CASCADE_OK) rc = upload_species(h, 1, n_posi, cell_p, off_p, u_p);
+  tr.mark(rc == CASCADE_OK ? h : nullptr, "species 1");
   if (rc == CASCADE_OK) rc = set_counts(h, n_elec, n_posi);
+  tr.mark(rc == CASCADE_OK ? h : nullptr, "counts");
   if (rc != CASCADE_OK) {
     cascade_destroy(h);
     return rc;
@@ -484,15 +522,21 @@ int cascade_create_from_state_f32(const cascade_params* params, int64_t n_elec, 
   if ((n_elec > 0 && (!cell_e || !off_e || !u_e)) || (n_posi > 0 && (!cell_p || !off_p || !u_p)))
     return CASCADE_ERR_INVALID_ARG;
   cascade_t* h = nullptr;
+  UploadTrace tr;
   int rc = setup(params, cuda_stream, &h);
+  tr.mark(rc == CASCADE_OK ? h : nullptr, "setup (allocations)");
   if (rc == CASCADE_OK && (n_elec > params->particle_cap || n_posi > params->particle_cap)) {
     snprintf(g_msg, sizeof(g_msg), "state exceeds particle_cap");
     rc = CASCADE_ERR_CAPACITY;
   }
   if (rc == CASCADE_OK) rc = upload_E(h, E_host);
+  tr.mark(rc == CASCADE_OK ? h : nullptr, "E");
   if (rc == CASCADE_OK) rc = upload_species(h, 0, n_elec, cell_e, off_e, u_e);
+  tr.mark(rc == CASCADE_OK ? h : nullptr, "species 0");
   if (rc == CASCADE_OK) rc = upload_species(h, 1, n_posi, cell_p, off_p, u_p);
+  tr.mark(rc == CASCADE_OK ? h : nullptr, "species 1");
   if (rc == CASCADE_OK) rc = set_counts(h, n_elec, n_posi);
+  tr.mark(rc == CASCADE_OK ? h : nullptr, "counts");
   if (rc != CASCADE_OK) {
     cascade_destroy(h);
     return rc;
@@ -559,6 +603,54 @@ int cascade_diag(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t* n
   if (n_out) *n_out = (int32_t)n;
   if (E_host && (rc = d2h(h, E_host, h->d.E, sizeof(double) * h->d.nx))) return rc;
   if (J_host && (rc = d2h(h, J_host, h->d.J, sizeof(double) * h->d.nx))) return rc;
+  return h->sticky;
+}
+
+int cascade_record_enqueue(cascade_t* h) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!h) return CASCADE_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  if (!h->h_rec) {
+    CUDA_TRY(cudaMallocHost(&h->h_rec, sizeof(Ctl) * kRecRing));
+    for (cudaEvent_t& e : h->ev_rec) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  const int k = (int)(h->rec_issued % kRecRing);
+  if (h->rec_issued - h->rec_read >= kRecRing) {
+    snprintf(g_msg, sizeof(g_msg), "%d record copies queued and not yet polled", kRecRing);
+    return CASCADE_ERR_BUSY;
+  }
+  // the whole control block: the newest record and the device's error flag
+  CUDA_TRY(cudaMemcpyAsync(&h->h_rec[k], h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaEventRecord(h->ev_rec[k], h->stream));
+  ++h->rec_issued;
+  return CASCADE_OK;
+}
+
+int32_t cascade_record_copy_bytes(void) { return (int32_t)sizeof(Ctl); }
+
+int cascade_record_poll(cascade_t* h, cascade_diag_t* out, int32_t max, int32_t wait, int32_t* n_out) {
+  g_msg[0] = '\0';  // a message describes this call only
+  if (!h || max < 0 || (max > 0 && !out) || !n_out) return CASCADE_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  int32_t n = 0;
+  while (n < max && h->rec_read < h->rec_issued) {
+    const int k = (int)(h->rec_read % kRecRing);
+    if (wait) {
+      CUDA_TRY(cudaEventSynchronize(h->ev_rec[k]));
+    } else {
+      const cudaError_t e = cudaEventQuery(h->ev_rec[k]);
+      if (e == cudaErrorNotReady) {
+        (void)cudaGetLastError();
+        break;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "record event");
+    }
+    const Ctl& c = h->h_rec[k];
+    if (c.err && !h->sticky) h->sticky = c.err;
+    out[n++] = c.last;
+    ++h->rec_read;
+  }
+  *n_out = n;
   return h->sticky;
 }
 
@@ -696,6 +788,9 @@ int cascade_destroy(cascade_t* h) {
   cudaSetDevice(h->device);
   if (h->stream || !h->allocs.empty()) cudaStreamSynchronize(h->stream);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_rec)
+    if (e) cudaEventDestroy(e);
+  if (h->h_rec) cudaFreeHost(h->h_rec);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void* ptr : h->allocs) {

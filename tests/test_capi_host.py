@@ -162,3 +162,10 @@ def test_batch_rejects_two_word_members():
         capi.cascade_batch_create(ps, 0, 0)
     assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
     assert "member 1: batch members keep one-word FP32 momenta" in str(ei.value)
+
+
+def test_record_copy_size():
+    """A queued record copy moves the control block: the 112-byte record
+    with the step's counters and the device error flag (256 B)."""
+    assert capi.cascade_record_copy_bytes() == 256
+    assert capi.cascade_record_copy_bytes() >= ctypes.sizeof(capi.cascade_diag_t)
