@@ -182,9 +182,10 @@ int cascade_diag(cascade_t* h, cascade_diag_t* host_out, int32_t max, int32_t* n
  * result while the next step runs).  cascade_record_enqueue queues, behind
  * the work queued on the cascade's stream so far, a copy of the newest
  * step's record (the one cascade_diag returns last) into pinned host memory
- * the library holds, and returns at once.  At most 64 copies may be queued
- * and not yet polled; a further call returns CASCADE_ERR_BUSY and queues
- * nothing.  cascade_record_poll hands back up to max queued records, oldest
+ * the library holds, and returns at once -- except when 64 copies are in
+ * flight: it then waits for the oldest (so the host runs at most 64 steps
+ * ahead of the device) and keeps that record for the poll.  Records are
+ * kept until polled.  cascade_record_poll hands back up to max queued records, oldest
  * first, into host_out: with wait = 0 those that have landed (possibly none,
  * *n_out = 0), with wait != 0 it waits for each one it returns.  Returns the
  * cascade's sticky error status, like cascade_diag. */

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <deque>
 #include <mutex>
 #include <new>
 #include <string>
@@ -136,6 +137,7 @@ struct cascade {
   Ctl* h_rec = nullptr;  // pinned, kRecRing copies of the control block
   cudaEvent_t ev_rec[kRecRing] = {};
   long long rec_issued = 0, rec_read = 0;
+  std::deque<cascade_diag_t> rec_landed;  // taken from a full ring, not yet polled
 
   void* dalloc(size_t n) {
     n = (n + 255) & ~size_t(255);
@@ -358,12 +360,16 @@ int upload_species(cascade_t* h, int s, long long n, const int32_t* cell, const 
   if (!stage) return CASCADE_ERR_OOM;
   UploadTrace tr;
   tr.mark(h, "  staging buffer");
+  // Measured: after a cascade that had stepped was destroyed, the copies
+  // below, queued without this wait, moved 3.7 GB in 135-160 ms; with it,
+  // in 20 ms.  The cause was not found; the wait costs microseconds.
+  cudaError_t e = cudaStreamSynchronize(h->stream);
   H* so = static_cast<H*>(stage);
   H* su = so + chunk;
   const int f32 = sizeof(H) == sizeof(float) ? 1 : 0;
   unsigned int* bad = reinterpret_cast<unsigned int*>(h->scalar);
   unsigned int nbad = 0;
-  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d.cell[s], cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream);
   for (long long k = 0; k < n && e == cudaSuccess; k += chunk) {
@@ -616,8 +622,13 @@ int cascade_record_enqueue(cascade_t* h) {
   }
   const int k = (int)(h->rec_issued % kRecRing);
   if (h->rec_issued - h->rec_read >= kRecRing) {
-    snprintf(g_msg, sizeof(g_msg), "%d record copies queued and not yet polled", kRecRing);
-    return CASCADE_ERR_BUSY;
+    // the ring is full: wait for its oldest copy (the host is then at most
+    // kRecRing steps ahead of the device) and keep that record for the poll
+    CUDA_TRY(cudaEventSynchronize(h->ev_rec[k]));
+    const Ctl& c = h->h_rec[k];
+    if (c.err && !h->sticky) h->sticky = c.err;
+    h->rec_landed.push_back(c.last);
+    ++h->rec_read;
   }
   // the whole control block: the newest record and the device's error flag
   CUDA_TRY(cudaMemcpyAsync(&h->h_rec[k], h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
@@ -633,6 +644,10 @@ int cascade_record_poll(cascade_t* h, cascade_diag_t* out, int32_t max, int32_t 
   if (!h || max < 0 || (max > 0 && !out) || !n_out) return CASCADE_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   int32_t n = 0;
+  while (n < max && !h->rec_landed.empty()) {
+    out[n++] = h->rec_landed.front();
+    h->rec_landed.pop_front();
+  }
   while (n < max && h->rec_read < h->rec_issued) {
     const int k = (int)(h->rec_read % kRecRing);
     if (wait) {
