@@ -1271,9 +1271,9 @@ int batch_tune_with_warmup(cascade_batch_t* b, long long* steps, long long warmu
 // What a batch member may not be: two-word FP32 momenta, or more particles
 // per species than the batched kernel's 32-bit chunk indices cover.
 int batch_member_params(const cascade_params* p) {
-  if (p->particle_cap > kIdx32MaxCap) {
+  if (p->particle_cap > kBatchMaxCap) {
     snprintf(g_msg, sizeof(g_msg), "batch members hold at most %lld particles per species (particle_cap %lld)",
-             (long long)kIdx32MaxCap, (long long)p->particle_cap);
+             (long long)kBatchMaxCap, (long long)p->particle_cap);
     return CASCADE_ERR_INVALID_ARG;
   }
   int words = 1;

@@ -108,12 +108,9 @@ struct BatchMember {
 };
 
 // Entries of the constant-bank member table in each kernel translation unit.
-// particles per species that 32-bit chunk and particle indices cover: the
-// batched kernels index with 32 bits (members are capped at this), and a
-// single cascade uses its 32-bit particle kernel when its cap is within it
-// (the conversions of a step never take a species past its cap, so a count
-// plus the step's conversions stays within the cap too)
-constexpr long long kIdx32MaxCap = 1LL << 30;
+// particles per species a batch member may hold: the batched kernel indexes
+// 4-particle chunks and particles of one member with 32-bit integers
+constexpr long long kBatchMaxCap = 1LL << 30;
 constexpr int kConstMembers = 64 * 1024 / sizeof(BatchMember) - 8;
 
 // A batch of cascades advanced together (one launch per kernel per step).

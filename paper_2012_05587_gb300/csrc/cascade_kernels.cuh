@@ -681,13 +681,10 @@ constexpr size_t kStageBytesPerThread = 2 * 3 * 16;
 // shared memory with cp.async while the current ones are processed, so each
 // thread keeps one iteration of loads in flight at all times.
 // COMP: two-word momenta (see process4); direct loads.
-// I32: chunk and particle indices in 32-bit integers, for cascades of at
-// most 2^30 particles per species (fewer instructions per iteration).
-template <class Real, int V, int DEP, bool FAST, bool OPEN, bool STG = false, bool COMP = false, bool I32 = false>
+template <class Real, int V, int DEP, bool FAST, bool OPEN, bool STG = false, bool COMP = false>
 __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
   static_assert(!STG || sizeof(Real) == 4, "the staging slots hold four 4-byte values");
   typedef typename AccOf<Real, DEP>::type Acc;
-  typedef typename std::conditional<I32, int, long long>::type Idx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   Ctl* ctl = d.ctl;
@@ -713,17 +710,17 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
   __syncthreads();
 
   const long long cc = ctl->conv_count;
-  const Idx N0 = (Idx)(ctl->n[0] + cc), N1 = (Idx)(ctl->n[1] + cc);
-  const Idx C0 = (N0 + 3) >> 2, C1 = (N1 + 3) >> 2, C = C0 + C1;
+  const long long N0 = ctl->n[0] + cc, N1 = ctl->n[1] + cc;
+  const long long C0 = (N0 + 3) >> 2, C1 = (N1 + 3) >> 2, C = C0 + C1;
   st.ph_tail = ctl->ph_tail;
   st.room = d.ph_cap - (st.ph_tail - ctl->conv_end);
   st.ph_mask = d.ph_cap - 1;
-  const Idx stride = (Idx)G * (Idx)blockDim.x;
-  const Idx first_wb = (Idx)blockIdx.x * (Idx)blockDim.x;
-  const Idx iters_cta = (C > first_wb) ? (C - first_wb + stride - 1) / stride : 0;
+  const long long stride = (long long)G * blockDim.x;
+  const long long first_wb = (long long)blockIdx.x * blockDim.x;
+  const long long iters_cta = (C > first_wb) ? (C - first_wb + stride - 1) / stride : 0;
   // every CTA takes the scale of the busiest one (CTA 0), so the int32 rows
   // of DEP 1 share one scale and the field kernel sums them exactly
-  const long long iters_max = ((long long)C + stride - 1) / stride;
+  const long long iters_max = (C + stride - 1) / stride;
   set_scales<Real, DEP>(st, (double)(iters_max * blockDim.x * 4), d.dtdx);
   if (DEP == 1 && blockIdx.x == 0 && threadIdx.x == 0) ctl->part_inv = st.fx_inv;
 
@@ -733,12 +730,12 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
   unsigned char* stage = smem_raw + smem_field_bytes<Real>(nx, V, DEP);
   const size_t slab = (size_t)blockDim.x * 16;
   auto slot = [&](int b, int a) { return stage + (size_t)(b * 3 + a) * slab + (size_t)threadIdx.x * 16; };
-  auto issue = [&](Idx it) {  // cp.async of iteration it's chunk into stage it & 1
-    const Idx ch = first_wb + it * stride + warp * 32 + lane;
+  auto issue = [&](long long it) {  // cp.async of iteration it's chunk into stage it & 1
+    const long long ch = first_wb + it * stride + warp * 32 + lane;
     if (it < iters_cta && ch < C) {
       const int sp = ch < C0 ? 0 : 1;
-      const Idx bp = (ch - (sp ? C0 : 0)) * 4;
-      const unsigned bytes = (unsigned)min((Idx)4, (sp ? N1 : N0) - bp) * 4u;
+      const long long bp = (ch - (sp ? C0 : 0)) * 4;
+      const unsigned bytes = (unsigned)min(4LL, (sp ? N1 : N0) - bp) * 4u;
       const int b = (int)(it & 1);
       cp_async16(slot(b, 0), d.cell[sp] + bp, bytes);
       cp_async16(slot(b, 1), static_cast<const Real*>(d.off[sp]) + bp, bytes);
@@ -749,9 +746,9 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
   if (STG) issue(0);
   double gsum_total = 0.0;
   const int pf = d.prefetch;  // iterations ahead that lane 0 prefetches its warp's particles
-  for (Idx it = 0; it < iters_cta; ++it) {
+  for (long long it = 0; it < iters_cta; ++it) {
     if (pf > 0 && lane == 0) {
-      const long long chp = first_wb + ((long long)it + pf) * stride + warp * 32;  // the warp's first chunk then
+      const long long chp = first_wb + (it + pf) * stride + warp * 32;  // the warp's first chunk then
       if (chp < C) {
         const int sp = chp < C0 ? 0 : 1;
         const long long bp = (chp - (sp ? C0 : 0)) * 4;
@@ -765,14 +762,14 @@ __global__ void __launch_bounds__(PushBlock<Real>::value, 1) k_push(Dev d) {
         }
       }
     }
-    const Idx ch = first_wb + it * stride + warp * 32 + lane;
+    const long long ch = first_wb + it * stride + warp * 32 + lane;
     int s = 0, cnt = 0;
-    Idx base = 0;
+    long long base = 0;
     if (ch < C) {
       s = ch < C0 ? 0 : 1;
       base = (ch - (s ? C0 : 0)) * 4;
-      const Idx N = s ? N1 : N0;
-      cnt = (int)min((Idx)4, N - base);
+      const long long N = s ? N1 : N0;
+      cnt = (int)min(4LL, N - base);
     }
     if (STG) {
       issue(it + 1);
@@ -1593,10 +1590,10 @@ __global__ void k_gauss_reduce(Dev d, double* rho_dx, double* out, int every = 0
 // accumulator.
 template <class Real>
 struct PushTable {
-  static const void* get(int V, int dep, bool fast, bool open, bool stage, bool comp = false, bool i32 = false);
+  static const void* get(int V, int dep, bool fast, bool open, bool stage, bool comp = false);
 };
 template <>
-inline const void* PushTable<double>::get(int V, int, bool, bool open, bool, bool, bool) {
+inline const void* PushTable<double>::get(int V, int, bool, bool open, bool, bool) {
   if (V == kSmemESmemS)
     return open ? reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false, true>)
                 : reinterpret_cast<const void*>(&k_push<double, kSmemESmemS, 0, false, false>);
@@ -1607,7 +1604,7 @@ inline const void* PushTable<double>::get(int V, int, bool, bool open, bool, boo
   return reinterpret_cast<const void*>(&k_push<double, kGlobEGlobS, 0, false, false>);
 }
 template <>
-inline const void* PushTable<float>::get(int V, int dep, bool, bool open, bool stage, bool comp, bool i32) {
+inline const void* PushTable<float>::get(int V, int dep, bool, bool open, bool stage, bool comp) {
   if (comp) {  // two-word momenta: the shared-memory accumulator forms, direct loads
     if (V == kSmemESmemS) {
       if (open) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, true, false, true>);
@@ -1622,8 +1619,7 @@ inline const void* PushTable<float>::get(int V, int dep, bool, bool open, bool s
   }
   if (V == kSmemESmemS) {
     if (stage && !open && dep == 1)
-      return i32 ? reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, false, true, false, true>)
-                 : reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, false, true>);
+      return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, false, true>);
     if (open) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, true>);
     if (dep == 4) return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 4, true, false>);
     return reinterpret_cast<const void*>(&k_push<float, kSmemESmemS, 1, true, false>);
@@ -1652,7 +1648,7 @@ struct Launchers {
 
   static const void* push_fn(const Dev& d) {
     return PushTable<Real>::get(d.variant, d.push_dep, d.push_fast != 0, d.open_bc != 0, d.push_stage != 0,
-                                sizeof(Real) == 4 && d.u_words == 2, d.cap4 <= kIdx32MaxCap);
+                                sizeof(Real) == 4 && d.u_words == 2);
   }
 
   static cudaError_t configure(Dev& d, int num_sms) {
