@@ -1021,7 +1021,7 @@ struct cascade_batch {
 namespace {
 
 constexpr int kTuneMaxSteps = 256;  // tuning steps logged per tuning pass
-constexpr int kConstCtasPerSm = 8;  // constant-bank batch kernel: working CTAs per SM and step (4: 2.15e11, 8: 2.24e11, 16: 2.24e11 on the 256-cascade scan)
+constexpr int kConstCtasPerSm = 16;  // constant-bank batch kernel: working CTAs per SM and step (256-cascade scan: 4: 2.33e11, 8: 2.41e11, 16: 2.43e11)
 
 // Launch parameters of one variant (no graph change); CASCADE_ERR_INVALID_ARG
 // when the variant does not fit this batch (staging beside a large grid, a
