@@ -348,44 +348,62 @@ int upload_E(cascade_t* h, const double* E_host) {
 template <class H>
 int upload_species(cascade_t* h, int s, long long n, const int32_t* cell, const H* off, const H* u) {
   if (n == 0) return CASCADE_OK;
-  const long long chunk = n < (1LL << 23) ? n : (1LL << 23);
-  const size_t stage_bytes = sizeof(H) * (size_t)chunk;
-  void* stage = nullptr;
-  if (h->alloc_fn) {
-    stage = h->alloc_fn(2 * stage_bytes, (void*)h->stream, h->alloc_ctx);
-  } else if (cudaMalloc(&stage, 2 * stage_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    stage = nullptr;
-  }
-  if (!stage) return CASCADE_ERR_OOM;
+  const int f32 = sizeof(H) == sizeof(float) ? 1 : 0;
+  unsigned int* bad = reinterpret_cast<unsigned int*>(h->scalar);
+  unsigned int nbad = 0;
   UploadTrace tr;
-  tr.mark(h, "  staging buffer");
   // Measured: after a cascade that had stepped was destroyed, the copies
   // below, queued without this wait, moved 3.7 GB in 135-160 ms; with it,
   // in 20 ms.  The cause was not found; the wait costs microseconds.
   cudaError_t e = cudaStreamSynchronize(h->stream);
-  H* so = static_cast<H*>(stage);
-  H* su = so + chunk;
-  const int f32 = sizeof(H) == sizeof(float) ? 1 : 0;
-  unsigned int* bad = reinterpret_cast<unsigned int*>(h->scalar);
-  unsigned int nbad = 0;
   if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d.cell[s], cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream);
-  for (long long k = 0; k < n && e == cudaSuccess; k += chunk) {
-    const long long m = (n - k) < chunk ? (n - k) : chunk;
-    e = cudaMemcpyAsync(so, off + k, sizeof(H) * m, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(su, u + k, sizeof(H) * m, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-      e = h->real_size == sizeof(double) ? upload_fp64(h->d, s, k, m, so, su, f32, bad, h->stream)
-                                         : upload_fp32(h->d, s, k, m, so, su, f32, bad, h->stream);
+  auto check = [&](long long first, long long m, const void* so, const void* su) {
+    return h->real_size == sizeof(double) ? upload_fp64(h->d, s, first, m, so, su, f32, bad, h->stream)
+                                          : upload_fp32(h->d, s, first, m, so, su, f32, bad, h->stream);
+  };
+  void* stage = nullptr;
+  if (sizeof(H) == h->real_size) {
+    // the host arrays hold the particle precision: straight into place,
+    // then checked there (the kernel reads and rewrites each element)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.off[s], off, sizeof(H) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.u[s], u, sizeof(H) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = check(0, n, h->d.off[s], h->d.u[s]);
+  } else {
+    // FP64 host arrays for an FP32 cascade: through a device staging buffer
+    // in chunks, rounded by the kernel
+    const long long chunk = n < (1LL << 23) ? n : (1LL << 23);
+    const size_t stage_bytes = sizeof(H) * (size_t)chunk;
+    if (e == cudaSuccess) {
+      if (h->alloc_fn) {
+        stage = h->alloc_fn(2 * stage_bytes, (void*)h->stream, h->alloc_ctx);
+      } else if (cudaMalloc(&stage, 2 * stage_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        stage = nullptr;
+      }
+      if (!stage) {
+        cudaStreamSynchronize(h->stream);
+        return CASCADE_ERR_OOM;
+      }
+    }
+    H* so = static_cast<H*>(stage);
+    H* su = so + chunk;
+    for (long long k = 0; k < n && e == cudaSuccess; k += chunk) {
+      const long long m = (n - k) < chunk ? (n - k) : chunk;
+      e = cudaMemcpyAsync(so, off + k, sizeof(H) * m, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(su, u + k, sizeof(H) * m, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = check(k, m, so, su);
+    }
   }
-  tr.mark(h, "  copies and rounding");
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (h->free_fn) h->free_fn(stage, (void*)h->stream, h->alloc_ctx);
-  else cudaFree(stage);
-  tr.mark(h, "  staging freed");
+  else cudaStreamSynchronize(h->stream);  // nothing queued may still use the staging buffer
+  tr.mark(h, "  copies and checks");
+  if (stage) {
+    if (h->free_fn) h->free_fn(stage, (void*)h->stream, h->alloc_ctx);
+    else cudaFree(stage);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "state upload");
   if (nbad) {
     snprintf(g_msg, sizeof(g_msg), "%u particles of species %d outside the grid or not finite", nbad, s);

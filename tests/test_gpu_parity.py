@@ -405,8 +405,9 @@ def test_per_step_gauss_residual_against_the_oracle(precision, rtol):
 def test_state_upload_from_fp32_host_arrays(precision):
     """cascade_create_from_state_f32 (12 B per particle from the host) gives
     the same particles as the FP64 form given the same, FP32-representable,
-    values, and the same steps after; values outside the grid are still
-    rejected."""
+    values, and the same steps after; values outside the grid or not finite
+    are still rejected, whether the host arrays go straight into place (the
+    cascade's own precision) or through the staging buffer."""
     p = dict(W.small_cascade(), precision=precision)
     with Cascade(dict(p, precision="fp32")) as c:
         c.step(30)
@@ -438,3 +439,12 @@ def test_state_upload_from_fp32_host_arrays(precision):
     with pytest.raises(CascadeError) as ei:
         Cascade(dict(p, particle_cap=64), state=bad)
     assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
+    # FP64 host arrays: an offset of 1 and a non-finite momentum, both counted
+    bad64 = {"elec": {"cell": np.array([3, 4]), "off": np.array([0.5, 1.0]), "u": np.array([0.0, 0.0])},
+             "posi": {"cell": np.array([3]), "off": np.array([0.5]), "u": np.array([np.nan])}}
+    for st in (bad64, {"elec": bad64["elec"], "posi": {"cell": np.array([3]), "off": np.array([0.5]),
+                                                        "u": np.array([0.0])}}):
+        with pytest.raises(CascadeError) as ei:
+            Cascade(dict(p, particle_cap=64), state=st)
+        assert ei.value.status == capi.CASCADE_ERR_INVALID_ARG
+        assert "outside the grid or not finite" in str(ei.value)
