@@ -333,7 +333,7 @@ enum { CASCADE_VARIANT_DEFAULT = 0, CASCADE_VARIANT_CACHED = 1, CASCADE_VARIANT_
  * real steps of the members' work.  Setting any of CASCADE_BATCH_SHAPE,
  * CASCADE_BATCH_STAGE, CASCADE_BATCH_PREFETCH, CASCADE_BATCH_MEMBER_COST
  * before creation forces a variant (no tuning); CASCADE_BATCH_TUNE=0 keeps
- * the default variant.  CASCADE_BATCH_CTAS_PER_SM (1..64, default 16) sets how
+ * the default variant.  CASCADE_BATCH_CTAS_PER_SM (1..64, default 8) sets how
  * many CTAs per SM and step shape 4 splits the members' work into.
  *   cascade_batch_set_variant  forces v (CASCADE_ERR_INVALID_ARG if it does not
  *                              fit this batch) and disarms tuning

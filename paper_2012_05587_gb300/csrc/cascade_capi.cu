@@ -1039,7 +1039,11 @@ struct cascade_batch {
 namespace {
 
 constexpr int kTuneMaxSteps = 256;  // tuning steps logged per tuning pass
-constexpr int kConstCtasPerSm = 16;  // constant-bank batch kernel: working CTAs per SM and step (256-cascade scan: 4: 2.33e11, 8: 2.41e11, 16: 2.43e11)
+// constant-bank batch kernel: working CTAs per SM and step.  256-cascade
+// scan, 3000 steps: 4: 2.33e11, 8: 2.41e11, 16: 2.43e11 particle-steps/s;
+// its first 300 steps (the growth phase): 8: 2.01e11, 16: 1.91e11 (at 16
+// the grid carries twice as many CTAs that find no work and exit)
+constexpr int kConstCtasPerSm = 8;
 
 // Launch parameters of one variant (no graph change); CASCADE_ERR_INVALID_ARG
 // when the variant does not fit this batch (staging beside a large grid, a
