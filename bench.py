@@ -107,7 +107,7 @@ def parse():
     ap.add_argument("--serve-low-requests", type=int, default=400)
     ap.add_argument("--fp64-sample", type=int, default=32,
                     help="cascades run one at a time in FP64 for comparison, spread evenly over the predicted "
-                         "particle-steps (0 = every scan member, or 64 requests when serving)")
+                         "particle-steps (0 = none, -1 = every scan member or request)")
     ap.add_argument("--paper-time", type=float, default=12.0, help="paper workload: simulated time (1/omega_p)")
     ap.add_argument("--paper-fs", default="0.1,0.01,0.004", help="paper workload: values of f")
     ap.add_argument("--paper-dt-factors", default="1", help="paper workload: multiples of the paper's time step")

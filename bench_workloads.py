@@ -47,8 +47,11 @@ def _fp64_one_at_a_time(params: list, steps_of) -> dict:
 
 def stratified(params: list, n: int, key) -> list:
     """n members spread evenly over ``params`` sorted by ``key`` (every size
-    class represented); all of them when n <= 0 or n >= len(params)."""
-    if n <= 0 or n >= len(params):
+    class represented); all of them when n < 0 or n >= len(params), none
+    when n == 0."""
+    if n == 0:
+        return []
+    if n < 0 or n >= len(params):
         return list(params)
     order = sorted(range(len(params)), key=lambda i: key(params[i]))
     return [params[order[int((k + 0.5) * len(params) / n)]] for k in range(n)]
@@ -131,6 +134,8 @@ def _gather(obj, world: int) -> list:
 
 
 def _sample_note(n_sample: int, n_all: int, what: str) -> str:
+    if n_sample == 0:
+        return f"not run (none of the {n_all} {what})"
     if n_sample >= n_all:
         return f"all {n_all} {what}, each alone in FP64"
     return (f"{n_sample} of {n_all} {what}, spread evenly over the predicted particle-steps "
@@ -436,8 +441,7 @@ def run_serve(args) -> int:
                        f"{args.serve_low_frac} of the capacity measured by the saturated run")
     if rank != 0:
         return 0
-    n_fp64 = args.fp64_sample if args.fp64_sample > 0 else 64
-    sample = stratified(reqs_all, n_fp64, lambda p: W.predicted_particles(p) * p["steps"])
+    sample = stratified(reqs_all, args.fp64_sample, lambda p: W.predicted_particles(p) * p["steps"])
     fp64 = _fp64_one_at_a_time(sample, lambda p: p["steps"])
     reqs = reqs_all
     line = {
@@ -455,9 +459,9 @@ def run_serve(args) -> int:
         "p99_time_to_result_s": sat["p99_time_to_result_s"],
         "saturated": {k: v for k, v in sat.items() if k not in ("ttr", "wait")},
         "below_capacity": low,
-        "fp64_alone": dict(fp64, p50_s=float(np.percentile(fp64["per_request_s"], 50)),
-                           p99_s=float(np.percentile(fp64["per_request_s"], 99)), per_request_s=None,
-                           sample=_sample_note(len(sample), len(reqs), "requests")),
+        "fp64_alone": dict(fp64, p50_s=float(np.percentile(fp64["per_request_s"], 50)) if sample else None,
+                           p99_s=float(np.percentile(fp64["per_request_s"], 99)) if sample else None,
+                           per_request_s=None, sample=_sample_note(len(sample), len(reqs), "requests")),
         "served_over_fp64_alone": sat["value"] / fp64["value"] if fp64["value"] else None,
         "clocks": clocks,
     }

@@ -118,3 +118,15 @@ def test_paired_comparison_reports_bias_and_its_error():
     c = A.paired_comparison(runs, refs)["x"]
     assert c["rel_err"] == pytest.approx(0.03, abs=0.003)
     assert 0.0 < c["rel_se"] < 0.002 and c["n"] == 400
+
+
+def test_stratified_sample_sizes():
+    import bench_workloads as BW
+
+    items = list(range(10))
+    assert BW.stratified(items, 0, lambda x: x) == []
+    assert BW.stratified(items, -1, lambda x: x) == items
+    assert BW.stratified(items, 20, lambda x: x) == items
+    got = BW.stratified(items, 5, lambda x: -x)  # sorted by key, spread evenly
+    assert len(got) == 5 and len(set(got)) == 5
+    assert got == [9, 7, 5, 3, 1]
