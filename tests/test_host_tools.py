@@ -129,4 +129,4 @@ def test_stratified_sample_sizes():
     assert BW.stratified(items, 20, lambda x: x) == items
     got = BW.stratified(items, 5, lambda x: -x)  # sorted by key, spread evenly
     assert len(got) == 5 and len(set(got)) == 5
-    assert got == [9, 7, 5, 3, 1]
+    assert got == [8, 6, 4, 2, 0]  # the middle of each fifth of [9, 8, ..., 0]
